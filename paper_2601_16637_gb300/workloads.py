@@ -1,0 +1,192 @@
+"""Seeded synthetic inputs for selected-basis diagonalization (SBD).
+
+This module only draws inputs: one-electron integrals h_pq, two-electron
+integrals (pq|rs) in chemists' notation, and the selected alpha/beta string
+sets A and B.  It holds none of the Hamiltonian arithmetic, so both the CUDA
+path and the CPU oracle can consume its output without sharing any of the
+method's code.
+
+The paper's own workload (Sec. IV: Fe4S4, 6,000 quantum-sampled 36-bit
+configurations, 3.6e7 determinants) is not available; these generators stand
+in for it with the same structure: a low-orbital-biased selected string set of
+fixed popcount, dense 8-fold-symmetric integrals and a product space A x B.
+
+Recipe (all numbers below are the workload definitions, not tunables):
+
+* h: symmetric; diagonal eps_p = -2 + 0.15 p; upper triangle off the diagonal
+  drawn N(0, (0.05 exp(-|p-q|/4))^2) and mirrored.
+* (pq|rs) = sum_{L < 2 norb} B^L_pq B^L_rs with B^L symmetric, its upper
+  triangle (diagonal included) iid N(0, 0.12^2) and mirrored.  The result is
+  positive semi-definite as a (pq),(rs) matrix and 8-fold symmetric.
+* strings: Gumbel-top-k sampling without replacement, the log-weight of a
+  string being -lam * sum of its occupied orbital indices.  The draw is exact
+  over the enumerated space when C(norb, n) <= 2^26; beyond that each string
+  is drawn as a Gumbel-top-n over orbitals (Plackett-Luce) and duplicates are
+  rejected, which is an approximation of the same bias.  The aufbau string
+  (lowest n orbitals occupied) is always included.  Strings are returned in
+  draw order (not sorted), so consumers exercise their own sorting.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+EXACT_ENUMERATION_LIMIT = 1 << 26
+
+# stream tags for np.random.default_rng([seed, tag])
+_TAG_H, _TAG_ERI, _TAG_A, _TAG_B = 0, 1, 2, 3
+
+
+@dataclass
+class Workload:
+    """One SBD instance: integrals, string sets and solve parameters."""
+
+    name: str
+    norb: int
+    nalpha: int
+    nbeta: int
+    h: np.ndarray            # [norb, norb] float64, symmetric
+    eri: np.ndarray          # [norb, norb, norb, norb] float64, (pq|rs)
+    A: np.ndarray            # [nA] uint64, alpha strings (draw order)
+    B: np.ndarray            # [nB] uint64, beta strings (draw order)
+    nroots: int = 1
+    tol: float = 1e-8
+    precision: str = "fp64"
+    max_subspace: int = 0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def ndets(self) -> int:
+        return int(self.A.size) * int(self.B.size)
+
+
+def one_electron(norb: int, seed: int) -> np.ndarray:
+    rng = np.random.default_rng([seed, _TAG_H])
+    h = np.zeros((norb, norb))
+    for p in range(norb):
+        h[p, p] = -2.0 + 0.15 * p
+    iu = np.triu_indices(norb, k=1)
+    sd = 0.05 * np.exp(-np.abs(iu[0] - iu[1]) / 4.0)
+    h[iu] = rng.normal(0.0, 1.0, size=sd.size) * sd
+    h[(iu[1], iu[0])] = h[iu]
+    return h
+
+
+def two_electron(norb: int, seed: int) -> np.ndarray:
+    rng = np.random.default_rng([seed, _TAG_ERI])
+    nl = 2 * norb
+    iu = np.triu_indices(norb)
+    Bl = np.zeros((nl, norb, norb))
+    for L in range(nl):
+        v = rng.normal(0.0, 0.12, size=iu[0].size)
+        Bl[L][iu] = v
+        Bl[L][(iu[1], iu[0])] = v
+    flat = Bl.reshape(nl, norb * norb)
+    eri = flat.T @ flat
+    return np.ascontiguousarray(eri.reshape(norb, norb, norb, norb))
+
+
+def all_strings(norb: int, n: int) -> np.ndarray:
+    """Every uint64 string with n of the low norb bits set (unsorted)."""
+    if not (0 <= n <= norb <= 64):
+        raise ValueError("need 0 <= n <= norb <= 64")
+    # level[k] = strings over bits [0, m) with k bits set
+    level = {0: np.zeros(1, dtype=np.uint64)}
+    for m in range(norb):
+        bit = np.uint64(1) << np.uint64(m)
+        nxt = {}
+        lo = max(0, n - (norb - m - 1))
+        for k in range(lo, min(n, m + 1) + 1):
+            parts = []
+            if k in level:
+                parts.append(level[k])
+            if k - 1 in level:
+                parts.append(level[k - 1] | bit)
+            if parts:
+                nxt[k] = np.concatenate(parts) if len(parts) > 1 else parts[0]
+        level = nxt
+    return level[n]
+
+
+def _orbital_sum(strings: np.ndarray, norb: int) -> np.ndarray:
+    tot = np.zeros(strings.size, dtype=np.float64)
+    for p in range(norb):
+        tot += p * ((strings >> np.uint64(p)) & np.uint64(1)).astype(np.float64)
+    return tot
+
+
+def gumbel_top_k(norb: int, n: int, k: int, lam: float, rng: np.random.Generator) -> np.ndarray:
+    """k distinct strings, log-weight -lam * sum(occupied indices)."""
+    total = math.comb(norb, n)
+    aufbau = np.uint64((1 << n) - 1) if n < 64 else np.uint64(0xFFFFFFFFFFFFFFFF)
+    if k >= total:
+        s = all_strings(norb, n)
+        return s[rng.permutation(s.size)]
+    if total <= EXACT_ENUMERATION_LIMIT:
+        s = all_strings(norb, n)
+        score = -lam * _orbital_sum(s, norb) + rng.gumbel(size=s.size)
+        top = np.argpartition(-score, k - 1)[:k]
+        top = top[np.argsort(-score[top], kind="stable")]
+        out = s[top]
+    else:
+        seen: dict[int, None] = {}
+        logw = -lam * np.arange(norb, dtype=np.float64)
+        while len(seen) < k:
+            batch = max(1024, 2 * (k - len(seen)))
+            g = logw[None, :] + rng.gumbel(size=(batch, norb))
+            occ = np.argpartition(-g, n - 1, axis=1)[:, :n]
+            bits = (np.uint64(1) << occ.astype(np.uint64))
+            strs = np.bitwise_or.reduce(bits, axis=1)
+            for x in strs.tolist():
+                if x not in seen:
+                    seen[x] = None
+                    if len(seen) == k:
+                        break
+        out = np.fromiter(seen.keys(), dtype=np.uint64, count=k)
+    if not np.any(out == aufbau):
+        out[-1] = aufbau
+    return out
+
+
+def make(name: str, norb: int, nalpha: int, nbeta: int, nA: int | None, nB: int | None,
+         lam: float, seed: int, **solve) -> Workload:
+    """Build one instance; nA/nB = None selects the full string space."""
+    h = one_electron(norb, seed)
+    eri = two_electron(norb, seed)
+    ra = np.random.default_rng([seed, _TAG_A])
+    rb = np.random.default_rng([seed, _TAG_B])
+    fullA, fullB = math.comb(norb, nalpha), math.comb(norb, nbeta)
+    A = gumbel_top_k(norb, nalpha, fullA if nA is None else nA, lam, ra)
+    B = gumbel_top_k(norb, nbeta, fullB if nB is None else nB, lam, rb)
+    return Workload(name, norb, nalpha, nbeta, h, eri, A, B, **solve)
+
+
+# The configurations the library is exercised and measured on.
+#   cfg1: full space norb=8, 4+4 electrons (4,900 determinants), 1 root, tol 1e-10
+#   cfg2: norb=16, 5+5, |A|=|B|=2,000 (4.0e6 determinants), lam 0.35, 3 roots, tol 1e-8
+#   cfg3: norb=29, 10+10, |A|=|B|=10,000 (1.0e8 determinants), lam 0.25, mixed precision,
+#         1 root, subspace <= 24
+CONFIGS = {
+    "cfg1": dict(norb=8, nalpha=4, nbeta=4, nA=None, nB=None, lam=0.0, seed=0,
+                 nroots=1, tol=1e-10, precision="fp64"),
+    "cfg2": dict(norb=16, nalpha=5, nbeta=5, nA=2000, nB=2000, lam=0.35, seed=1,
+                 nroots=3, tol=1e-8, precision="fp64"),
+    "cfg3": dict(norb=29, nalpha=10, nbeta=10, nA=10000, nB=10000, lam=0.25, seed=2,
+                 nroots=1, tol=1e-6, precision="mixed", max_subspace=24),
+}
+
+
+def config(name: str, **override) -> Workload:
+    spec = dict(CONFIGS[name])
+    spec.update(override)
+    return make(name, **spec)
+
+
+def random_vector(n: int, seed: int, nvec: int = 1) -> np.ndarray:
+    """Normalised N(0,1) test amplitudes, shape [nvec, n] float64."""
+    rng = np.random.default_rng([seed, 100])
+    x = rng.normal(size=(nvec, n))
+    x /= np.linalg.norm(x, axis=1, keepdims=True)
+    return x
