@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark: selected-basis diagonalization on the norb=29 workload.
+
+Workload (the largest single-instance configuration): norb = 29, 10 alpha +
+10 beta electrons, |A| = |B| = 10,000 Gumbel-top-k strings (orbital weights
+exp(-0.25 p)), 1.0e8 determinants, synthetic integrals (see
+paper_2601_16637_gb300/workloads.py).  One step = one complete solve through
+the C ABI: sbd_create (string sort/validation, excitation tables, string
+matrix elements, Hamiltonian diagonal) + sbd_davidson (lowest root, mixed
+precision sigma with FP64 defect correction, residual <= 1e-6) +
+sbd_destroy.  Inputs are resident in HBM when the timed region starts.
+
+value  = sigma=Hc determinant throughput of the whole step:
+         N * (sigma vector applications in the step) / step time, summed
+         over ranks (replicas: each GPU solves its own instance).
+e2e    = the same through the same calls with pinned HOST inputs and the
+         eigenvector written to pinned HOST memory (copies inside the timing).
+roofline = the dominant kernel of the step, timed with CUDA events recorded
+         by the library on the stream it launches on.
+cpu_baseline = the CPU oracle (tests-only code) timed on a bounded sample of
+         sigma rows of the same workload on this host's cores.
+
+`--impl reference` times that oracle alone (the CPU reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "σ=Hc dets/s"
+UNIT = "dets/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
+NUM_SMS = 152
+FP32_LANES_PER_SM = 128
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def workload_config(wl, precision):
+    return {"workload": f"{wl.name}: norb={wl.norb}, nalpha=nbeta={wl.nalpha}, |A|=|B|={wl.A.size:,} "
+                        f"Gumbel-top-k strings, {wl.ndets:.2e} determinants, {wl.nroots} root, "
+                        f"{precision} sigma + FP64 defect correction, residual <= {wl.tol:g}",
+            "norb": wl.norb, "nalpha": wl.nalpha, "nbeta": wl.nbeta, "nA": int(wl.A.size), "nB": int(wl.B.size),
+            "ndets": int(wl.ndets), "nroots": wl.nroots, "tol": wl.tol, "precision": precision,
+            "step": "sbd_create + sbd_davidson + sbd_destroy (one full solve)",
+            "l2": "inputs larger than L2 (C is 0.4-0.8 GB per vector, L2 129 MB)"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (tests-only code; timed here as the reported baseline)
+
+
+def oracle_rows_rate(wl, budget_s: float, seed: int = 0):
+    from oracle import oracle as O
+
+    O.build()
+    o = O.Oracle.from_workload(wl)
+    x = np.random.default_rng([seed, 7]).normal(size=(1, o.N))
+    x /= np.linalg.norm(x)
+    rng = np.random.default_rng(seed)
+    threads = O.num_threads()
+    pilot = rng.integers(0, o.N, size=max(8, 2 * threads))
+    t0 = time.perf_counter()
+    o.sigma_rows(x, pilot)
+    per_row = (time.perf_counter() - t0) / pilot.size
+    nrows = int(max(pilot.size, min(200000, budget_s / max(per_row, 1e-9))))
+    rows = rng.integers(0, o.N, size=nrows)
+    t0 = time.perf_counter()
+    o.sigma_rows(x, rows)
+    dt = time.perf_counter() - t0
+    o.close()
+    return nrows / dt, nrows, dt, threads
+
+
+def run_reference(args):
+    rank, _, world = env_rank()
+    if rank != 0:
+        return 0
+    from paper_2601_16637_gb300 import workloads as W
+
+    wl = W.config(args.workload)
+    precision = wl.precision
+    budget = args.ref_step_seconds
+    for _ in range(args.warmup):
+        oracle_rows_rate(wl, min(2.0, budget), seed=1)
+    vals, rows_total, t_total, threads = [], 0, 0.0, 1
+    for k in range(args.steps):
+        v, nrows, dt, threads = oracle_rows_rate(wl, budget, seed=100 + k)
+        vals.append(v)
+        rows_total += nrows
+        t_total += dt
+    value = rows_total / t_total
+    sample = (f"{args.steps} steps x ~{budget:g} s: {rows_total} sigma rows sampled uniformly from the "
+              f"{wl.ndets:.1e} determinants (each row = one determinant's sigma element)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(wl, precision),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+
+def traffic_record(kernel: str):
+    """dram bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = os.path.join(ROOT, "paper_2601_16637_gb300", "csrc", "sigma.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:
+            return float(parts[2])
+    return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg3")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample budget for cpu_baseline")
+    ap.add_argument("--ref-step-seconds", type=float, default=8.0)
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    from paper_2601_16637_gb300 import binding as B
+    from paper_2601_16637_gb300 import workloads as W
+
+    rank, local_rank, world = env_rank()
+    if world != args.gpus:
+        world = max(world, 1)
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    B.load(build_if_missing=True)
+    wl = W.config(args.workload)
+    prec = wl.precision
+    peaks, peak_src = load_peaks()
+    stream = torch.cuda.current_stream()
+
+    # inputs resident in HBM
+    h_d = torch.from_numpy(wl.h).cuda()
+    eri_d = torch.from_numpy(wl.eri).cuda()
+    A_d = torch.from_numpy(wl.A.view(np.int64)).cuda()
+    B_d = torch.from_numpy(wl.B.view(np.int64)).cuda()
+    vec_d = torch.empty((wl.nroots, wl.ndets), dtype=torch.float64, device="cuda")
+    alloc = B._TorchAllocator()
+
+    def options(timing=True):
+        o = B.sbd_default_options()
+        o.max_subspace = wl.max_subspace
+        o.timing = int(timing)
+        o.alloc, o.free = alloc.alloc, alloc.free
+        return o
+
+    def step(h, eri, A, Bs, vec, precision=prec):
+        handle = B.sbd_create(wl.norb, wl.nalpha, wl.nbeta, h, eri, A, Bs, options(), stream)
+        e = np.empty(wl.nroots)
+        r = np.empty(wl.nroots)
+        rc, rep = B.sbd_davidson(handle, wl.nroots, wl.tol, precision, e, vec, r)
+        ms, n = B.sbd_kernel_times(handle)
+        B.sbd_destroy(handle)
+        return e, r, rep.as_dict(), ms, n
+
+    for _ in range(args.warmup):
+        step(h_d, eri_d, A_d, B_d, vec_d)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = B.sbd_launch_count()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    reports, kms, kn, energies, resid = [], None, None, None, None
+    for _ in range(args.steps):
+        energies, resid, rep, ms, n = step(h_d, eri_d, A_d, B_d, vec_d)
+        reports.append(rep)
+        if kms is None:
+            kms, kn = ms, n
+        else:
+            for p in ms:
+                for k in ms[p]:
+                    kms[p][k] += ms[p][k]
+                    kn[p][k] += n[p][k]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = B.sbd_launch_count() - launches0
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    elapsed_max = max_over_ranks(elapsed, world)
+    n_sigma = sum(r["sigma_fp64"] + r["sigma_mixed"] for r in reports)
+    dets_all = sum_over_ranks(float(wl.ndets) * n_sigma, world)
+    value = dets_all / elapsed_max
+    solves_per_s = sum_over_ranks(float(args.steps), world) / elapsed_max
+
+    # per-kernel device times of the sigma kernels (events on the launch stream)
+    p_main = "mixed" if prec == "mixed" else "fp64"
+    kern = {p: {k: {"ms_total": kms[p][k], "launches": kn[p][k],
+                    "ms_per_launch": (kms[p][k] / kn[p][k]) if kn[p][k] else None} for k in kms[p]} for p in kms}
+    dominant = max(kms[p_main], key=lambda k: kms[p_main][k])
+    # algorithmic work per launch (multiply-adds of the sparse contraction, 2 FLOP each)
+    handle = B.sbd_create(wl.norb, wl.nalpha, wl.nbeta, h_d, eri_d, A_d, B_d, options(False), stream)
+    nsA, ndA = B.sbd_table_size(handle, 0, 1), B.sbd_table_size(handle, 0, 2)
+    nsB, ndB = B.sbd_table_size(handle, 1, 1), B.sbd_table_size(handle, 1, 2)
+    nA, nB = B.sbd_dims(handle)
+    elem = 4 if p_main == "mixed" else 8
+    flops = {"ab_pass": 2.0 * nsA * nsB,
+             "beta_pass": 2.0 * nA * (2 * nsB + ndB) + 2.0 * nA * nB,
+             "alpha_pass": 2.0 * nB * (2 * nsA + ndA)}
+    bytes_per_launch = {"transpose": 2.0 * nA * nB * elem}
+    ms_dom = kern[p_main][dominant]["ms_per_launch"]
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    if dominant == "transpose":
+        achieved = bytes_per_launch["transpose"] / (ms_dom * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s"}
+    else:
+        if p_main == "mixed":
+            peak_tf = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        else:
+            peak_tf = FP64_NOMINAL_TFLOPS
+        achieved = flops[dominant] / (ms_dom * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = f"{dominant} ({p_main})"
+    roof["peak_source"] = (f"{peak_src} HBM copy" if roof["bound"] == "hbm" else
+                           ("FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x max SM clock" if p_main == "mixed"
+                            else "nominal FP64 1.25 TFLOP/s"))
+    tr = traffic_record(f"{dominant}_{p_main}")
+    roof["traffic"] = tr
+
+    # sigma-only throughput by precision (sum of the four sigma kernels per vector)
+    sigma_rate = {}
+    for p in ("fp64", "mixed"):
+        tot = sum(kms[p].values())
+        nv = kn[p]["ab_pass"]
+        if nv:
+            sigma_rate[p] = wl.ndets * nv / (tot * 1e-3)
+
+    # FP64 comparison solve (outside the timed region)
+    mixed_vs_fp64 = None
+    if not args.no_fp64_compare and prec == "mixed":
+        e64, r64, rep64, ms64, n64 = step(h_d, eri_d, A_d, B_d, vec_d, precision="fp64")
+        sigma_rate.setdefault("fp64", wl.ndets * n64["fp64"]["ab_pass"] / (sum(ms64["fp64"].values()) * 1e-3))
+        mixed_vs_fp64 = {"E_mixed": float(energies[0]), "E_fp64": float(e64[0]),
+                         "abs_diff_Ha": float(abs(energies[0] - e64[0])),
+                         "solve_s_mixed": reports[-1]["seconds_total"], "solve_s_fp64": rep64["seconds_total"],
+                         "speedup": rep64["seconds_total"] / reports[-1]["seconds_total"]}
+    B.sbd_destroy(handle)
+
+    # end to end: pinned host inputs, eigenvector back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        h_h = torch.from_numpy(wl.h).pin_memory()
+        eri_h = torch.from_numpy(wl.eri).pin_memory()
+        A_h = torch.from_numpy(wl.A.view(np.int64)).pin_memory()
+        B_h = torch.from_numpy(wl.B.view(np.int64)).pin_memory()
+        vec_h = torch.empty((wl.nroots, wl.ndets), dtype=torch.float64, pin_memory=True)
+        step(h_h, eri_h, A_h, B_h, vec_h)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        n_sig_e2e = 0
+        for _ in range(args.steps):
+            _, _, rep, _, _ = step(h_h, eri_h, A_h, B_h, vec_h)
+            n_sig_e2e += rep["sigma_fp64"] + rep["sigma_mixed"]
+        torch.cuda.synchronize()
+        te = max_over_ranks(time.perf_counter() - t0, world)
+        h2d = wl.h.nbytes + wl.eri.nbytes + wl.A.nbytes + wl.B.nbytes
+        d2h = vec_h.numel() * 8 + wl.nroots * 8 * 2
+        e2e = {"value": sum_over_ranks(float(wl.ndets) * n_sig_e2e, world) / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        rate, nrows, dt, threads = oracle_rows_rate(wl, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{nrows} sigma rows sampled uniformly from the {wl.ndets:.1e} determinants "
+                         f"({dt:.1f} s); each row is one determinant's sigma element"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == "mixed" else "f64",
+                "data": "synthetic", "config": workload_config(wl, prec),
+                "parallelism": "replicas" if world > 1 else "single GPU",
+                "solves_per_s": solves_per_s, "sigma_applications_per_step": n_sigma / args.steps,
+                "sigma_only_dets_per_s": sigma_rate, "energy_Ha": float(energies[0]),
+                "residual": float(resid[0]), "kernels": kern, "mixed_vs_fp64": mixed_vs_fp64,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk, "last_report": reports[-1]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,222 @@
+/*
+ * sbd.h -- C ABI of the GB300 selected-basis diagonalization (SBD) library.
+ *
+ * The library computes, on one CUDA device, the lowest eigenpairs of the
+ * Hamiltonian restricted to a selected determinant space (paper Sec. II,
+ * Eqs. 1-2).  Determinants are the product A x B of a selected alpha-string
+ * set A and a selected beta-string set B ("half-bitstring" form, Sec. II-F):
+ * each string is a uint64 occupation bitstring over norb <= 64 spatial
+ * orbitals.  Amplitude vectors are stored row-major as C[|A|][|B|]
+ * (index ia*|B| + ib) with both string sets in ascending unsigned order.
+ *
+ * The Hamiltonian is Eq. 3 with one-electron integrals h_pq and
+ * two-electron integrals (pq|rs) in chemists' notation, i.e.
+ *   H = sum_pq h_pq E_pq + 1/2 sum_pqrs (pq|rs) (E_pq E_rs - delta_qr E_ps),
+ * E_pq = sum_spin a+_p a_q; matrix elements follow the Slater-Condon rules
+ * (Eq. 4).  Fermionic phases use the Jordan-Wigner order "all alpha modes
+ * ascending, then all beta modes ascending".
+ *
+ * Conventions for every entry point:
+ *  - Return value: 0 = SBD_OK, > 0 = warning, < 0 = error (enum below).
+ *    No C++ exception crosses the ABI.  sbd_last_error() describes the most
+ *    recent failure on the handle (or, for a NULL handle, on this thread).
+ *  - "device pointer": memory the CUDA runtime can address on the handle's
+ *    device.  "host or device pointer": any pointer cudaMemcpy can read with
+ *    cudaMemcpyDefault (pageable or pinned host memory, or device memory).
+ *  - Streams are cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  Work is enqueued on that stream; functions that return host
+ *    results synchronise it.
+ *  - A handle is not thread-safe: one host thread at a time per handle.
+ *  - Device memory owned by a handle comes from the allocator in
+ *    sbd_options (default: the CUDA stream-ordered allocator) and is freed by
+ *    sbd_destroy.  Caller-owned buffers stay caller-owned.
+ */
+#ifndef SBD_H
+#define SBD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sbd_ctx *sbd_handle;
+
+typedef enum {
+    SBD_FP64 = 0,  /* FP64 amplitudes, integrals, products and sums */
+    SBD_MIXED = 1, /* FP32 amplitudes and integrals, FP32 products and inner
+                      sums, FP64 accumulation per output element */
+} sbd_precision;
+
+enum {
+    SBD_OK = 0,
+    SBD_NOT_CONVERGED = 1,        /* warning: best estimates were still written */
+    SBD_ERR_INVALID_ARG = -1,     /* NULL pointer, size or count out of range */
+    SBD_ERR_BAD_STRING = -2,      /* popcount != electron count, or a bit >= norb */
+    SBD_ERR_DUPLICATE_STRING = -3,/* a string occurs twice in A or in B */
+    SBD_ERR_NORB = -4,            /* norb outside 1..64 */
+    SBD_ERR_OUT_OF_MEMORY = -5,   /* the allocator returned NULL */
+    SBD_ERR_OVER_BUDGET = -6,     /* would exceed sbd_options.hbm_budget_bytes */
+    SBD_ERR_CUDA = -7,            /* a CUDA runtime call failed */
+    SBD_ERR_NONFINITE = -8,       /* NaN or Inf in h or eri */
+    SBD_ERR_BREAKDOWN = -9,       /* Davidson could not extend its subspace */
+    SBD_ERR_UNSUPPORTED = -10,    /* a size this build does not handle */
+};
+
+/* Device allocator hooks.  alloc returns a device pointer (16-byte aligned
+ * or better) usable on `stream`, or NULL; free releases it, stream-ordered. */
+typedef void *(*sbd_alloc_fn)(void *ctx, size_t bytes, void *stream);
+typedef void (*sbd_free_fn)(void *ctx, void *ptr, void *stream);
+
+typedef struct {
+    double delta;            /* preconditioner floor delta of Eq. 7 (default 1e-4) */
+    int max_subspace;        /* Davidson subspace cap; 0 = max(24, 8*nroots), lowered to fit the budget */
+    int max_iter;            /* Davidson iteration cap; 0 = 200 */
+    size_t hbm_budget_bytes; /* cap on device bytes the handle may hold; 0 = unlimited */
+    double ecore;            /* constant added to reported energies */
+    int table_algo;          /* excitation tables: 0 auto, 1 all-pairs XOR-popcount, 2 enumerate + lookup */
+    int verbose;             /* > 0: per-iteration log on stderr */
+    sbd_alloc_fn alloc;      /* NULL: cudaMallocAsync / cudaFreeAsync */
+    sbd_free_fn free;
+    void *alloc_ctx;
+    int timing;              /* nonzero: time every sigma kernel with CUDA events (sbd_kernel_times) */
+} sbd_options;
+
+typedef struct {
+    int iterations;       /* Davidson iterations (all phases) */
+    int sigma_fp64;       /* vectors multiplied by the FP64 sigma */
+    int sigma_mixed;      /* vectors multiplied by the mixed sigma */
+    int restarts;         /* subspace restarts */
+    int refinements;      /* FP64 defect-correction steps (mixed mode) */
+    int status;           /* same as the return value */
+    double max_residual;  /* largest final residual norm (FP64-evaluated) */
+    double seconds_total; /* wall time inside sbd_davidson */
+    double seconds_sigma; /* of which sigma launches (host-timed with events) */
+} sbd_report;
+
+/* Fills *opt with the defaults listed above. */
+void sbd_default_options(sbd_options *opt);
+
+/* Human-readable name of a status code (static storage). */
+const char *sbd_status_string(int status);
+
+/*
+ * sbd_create -- build one instance (paper Sec. II-B/F, III-B).
+ *   norb        number of spatial orbitals, 1..64
+ *   nalpha/nbeta electrons per spin, 0..norb
+ *   h           host or device pointer, norb*norb doubles, row-major h[p*norb+q], symmetric
+ *   eri         host or device pointer, norb^4 doubles, (pq|rs) at ((p*norb+q)*norb+r)*norb+s,
+ *               8-fold symmetric (real orbitals)
+ *   A, B        host or device pointers, nA and nB uint64 strings in any order
+ *   opt         NULL for defaults
+ *   stream      cudaStream_t used for the build and as the handle's default stream
+ * The strings are validated (popcount, bits below norb, no duplicates), sorted
+ * ascending, and the excitation tables, string matrix elements and the
+ * Hamiltonian diagonal are built on the device.  The inputs are copied; the
+ * caller keeps ownership.  On error *out is NULL and nothing is leaked.
+ */
+int sbd_create(sbd_handle *out, int norb, int nalpha, int nbeta, const double *h, const double *eri,
+               const uint64_t *A, int64_t nA, const uint64_t *B, int64_t nB, const sbd_options *opt,
+               void *stream);
+
+/* Releases every device buffer of the handle (stream-ordered on its stream). */
+int sbd_destroy(sbd_handle handle);
+
+/* |A| and |B|; either output may be NULL. */
+int sbd_dims(sbd_handle handle, int64_t *nA, int64_t *nB);
+
+/* Device bytes currently held by the handle. */
+int sbd_memory(sbd_handle handle, size_t *bytes);
+
+/* Copies the sorted strings of one spin (0 alpha, 1 beta) to host memory
+ * (nA or nB uint64).  Synchronises the handle's stream. */
+int sbd_sorted_strings(sbd_handle handle, int spin, uint64_t *out_host);
+
+/*
+ * Excitation tables (paper Sec. III-B, the per-string singles/doubles lists).
+ * kind 1 = single, 2 = double excitations within one spin's sorted set.
+ * Canonical CSR: entries of source i at [ptr[i], ptr[i+1]), targets j
+ * ascending, no self entry.  orbs[4e..4e+3] = p1, p2, q1, q2 where p's are
+ * occupied in string i only and q's in string j only, each pair ascending
+ * (singles: p2 = q2 = 255).  sign = <S_i| a+_p1 a+_p2 a_q2 a_q1 |S_j> (singles:
+ * <S_i| a+_p a_q |S_j>).  sbd_table_size gives the entry count; sbd_tables
+ * copies to host buffers of ptr[n+1] (int64), target[m] (int32),
+ * orbs[4m] (uint8), sign[m] (int8); any of them may be NULL.
+ */
+int sbd_table_size(sbd_handle handle, int spin, int kind, int64_t *nentries);
+int sbd_tables(sbd_handle handle, int spin, int kind, int64_t *ptr_host, int32_t *target_host,
+               uint8_t *orbs_host, int8_t *sign_host);
+
+/*
+ * Same-spin string matrix elements <S_i|H_spin|S_j> (the Slater-Condon rules
+ * of Eq. 4 for one spin species alone), FP64, copied to host:
+ * kind 0: the diagonal, n values; kind 1/2: aligned with the entries of
+ * sbd_tables(spin, kind).
+ */
+int sbd_string_elements(sbd_handle handle, int spin, int kind, double *out_host);
+
+/* Hamiltonian diagonal H_ii (Sec. II-E, Eq. 5), nA*nB doubles, into a
+ * caller-owned device buffer, enqueued on `stream`. */
+int sbd_diagonal(sbd_handle handle, double *hd_dev, void *stream);
+
+/*
+ * Index lookup of strings in one spin's sorted set: idx[k] = position of
+ * keys[k], or -1 when absent (warp-cooperative search).  keys_dev and
+ * idx_dev are device pointers of n elements; enqueued on `stream`.
+ */
+int sbd_lookup(sbd_handle handle, int spin, const uint64_t *keys_dev, int64_t n, int64_t *idx_dev,
+               void *stream);
+
+/*
+ * sbd_sigma -- sigma = H c for nvec vectors (paper Sec. II-B Eq. 4; the
+ * matrix-free product of Sec. II-A), enqueued on `stream`.
+ *   c_dev     device pointer, [nvec][nA][nB], double for SBD_FP64 and float
+ *             for SBD_MIXED, in sorted-string order
+ *   sigma_dev device pointer, [nvec][nA][nB] doubles (written, not accumulated)
+ * The handle keeps one transposed copy of a vector as work space (allocated
+ * on the first call).  c and sigma must not overlap.
+ */
+int sbd_sigma(sbd_handle handle, const void *c_dev, double *sigma_dev, int nvec, sbd_precision prec,
+              void *stream);
+
+/*
+ * sbd_davidson -- lowest nroots eigenpairs by block Davidson (paper Sec. II-C
+ * with the damped diagonal preconditioner of Sec. II-E, stopping per
+ * Sec. II-G), on the handle's stream.
+ *   tol         residual-norm tolerance ||H u - theta u||_2 per root (u normalised)
+ *   prec        SBD_FP64, or SBD_MIXED: mixed-precision sigma for the bulk of the
+ *               iterations with FP64 defect correction (the converged residual is
+ *               always FP64-evaluated); orthogonalisation, the projected
+ *               eigenproblem, residuals and energies stay FP64
+ *   energies_host  nroots doubles (ascending), ecore included
+ *   vecs        NULL, or host or device pointer for [nroots][nA*nB] doubles
+ *   residuals_host NULL or nroots doubles
+ *   report      NULL or filled on return
+ * Returns SBD_OK, SBD_NOT_CONVERGED (estimates still written) or an error.
+ */
+int sbd_davidson(sbd_handle handle, int nroots, double tol, sbd_precision prec, double *energies_host,
+                 double *vecs, double *residuals_host, sbd_report *report);
+
+/*
+ * Per-kernel device time of the sigma kernels launched on this handle since
+ * the last reset (only when sbd_options.timing was set), measured with CUDA
+ * events recorded on the stream each kernel was launched on.  Slots:
+ *   0 transpose of C, 1 beta gather pass (rows of C), 2 alpha gather pass
+ *   (rows of C^T), 3 alpha-beta pass; FP64 kernels in 0..3, mixed in 4..7.
+ * ms_host and launches_host: 8 entries each (either may be NULL).  Waits for
+ * the recorded events; reset != 0 clears the counters afterwards.
+ */
+int sbd_kernel_times(sbd_handle handle, double *ms_host, int64_t *launches_host, int reset);
+
+/* Number of kernels this library has launched in the process so far. */
+int64_t sbd_launch_count(void);
+
+/* Message for the last failure on `handle` (NULL: on this thread); valid
+ * until the next call on the same handle / thread. */
+const char *sbd_last_error(sbd_handle handle);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBD_H */

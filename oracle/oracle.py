@@ -79,6 +79,8 @@ def load(mutation: int = 0) -> C.CDLL:
                                         _f64p, _f64p]
         lib.oracle_davidson.restype = C.c_int
         lib.oracle_num_threads.restype = C.c_int
+        lib.oracle_csr_counts.argtypes = [_p, _i64p]
+        lib.oracle_csr_fill.argtypes = [_p, _i64p, _i64p, _f64p]
         _libs[mutation] = lib
         return lib
 
@@ -142,6 +144,19 @@ class Oracle:
         out = np.empty(self.N * self.N)
         self.lib.oracle_dense(self._h, out)
         return out.reshape(self.N, self.N)
+
+    def csr(self):
+        """The Hamiltonian as a scipy CSR matrix (every H_ij of the space within two differences)."""
+        import scipy.sparse as sp
+
+        counts = np.empty(self.N, dtype=np.int64)
+        self.lib.oracle_csr_counts(self._h, counts)
+        ptr = np.zeros(self.N + 1, dtype=np.int64)
+        np.cumsum(counts, out=ptr[1:])
+        cols = np.empty(ptr[-1], dtype=np.int64)
+        vals = np.empty(ptr[-1])
+        self.lib.oracle_csr_fill(self._h, ptr, cols, vals)
+        return sp.csr_matrix((vals, cols, ptr), shape=(self.N, self.N))
 
     def sigma(self, x: np.ndarray) -> np.ndarray:
         x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)

@@ -392,6 +392,81 @@ void oracle_sigma_rows(void *p, const double *x, int nvec, const int64_t *rows, 
     }
 }
 
+/* The explicit Hamiltonian in CSR form (Sec. II-A, "explicit assembly"):
+ * row i lists every determinant j of the space within two spin-orbital
+ * differences (including i itself) with H_ij, in the enumeration order of
+ * oracle_sigma_rows.  oracle_csr_counts fills counts[i]; oracle_csr_fill
+ * writes cols/vals at ptr[i] (ptr = exclusive prefix of the counts). */
+static void row_neighbours(const oracle_t *o, int64_t i, int64_t **la, int64_t **lb, int64_t *na_, int64_t *nb_)
+{
+    det_t di = det_of(o, i);
+    for (int l = 0; l < 3; ++l) {
+        na_[l] = reachable(o->A, o->nA, o->norb, di.w[0], l, la[l]);
+        nb_[l] = reachable(o->B, o->nB, o->norb, di.w[1], l, lb[l]);
+    }
+}
+
+void oracle_csr_counts(void *p, int64_t *counts)
+{
+    oracle_t *o = (oracle_t *)p;
+    int64_t N = o->nA * o->nB;
+    int64_t capA = max_reachable(o->norb, o->na), capB = max_reachable(o->norb, o->nb);
+#pragma omp parallel
+    {
+        int64_t *la[3], *lb[3], na_[3], nb_[3];
+        for (int l = 0; l < 3; ++l) {
+            la[l] = (int64_t *)malloc((size_t)capA * sizeof(int64_t));
+            lb[l] = (int64_t *)malloc((size_t)capB * sizeof(int64_t));
+        }
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < N; ++i) {
+            row_neighbours(o, i, la, lb, na_, nb_);
+            int64_t c = 0;
+            for (int lA = 0; lA <= 2; ++lA)
+                for (int lB = 0; lA + lB <= 2; ++lB) c += na_[lA] * nb_[lB];
+            counts[i] = c;
+        }
+        for (int l = 0; l < 3; ++l) {
+            free(la[l]);
+            free(lb[l]);
+        }
+    }
+}
+
+void oracle_csr_fill(void *p, const int64_t *ptr, int64_t *cols, double *vals)
+{
+    oracle_t *o = (oracle_t *)p;
+    int64_t N = o->nA * o->nB;
+    int64_t capA = max_reachable(o->norb, o->na), capB = max_reachable(o->norb, o->nb);
+#pragma omp parallel
+    {
+        int64_t *la[3], *lb[3], na_[3], nb_[3];
+        for (int l = 0; l < 3; ++l) {
+            la[l] = (int64_t *)malloc((size_t)capA * sizeof(int64_t));
+            lb[l] = (int64_t *)malloc((size_t)capB * sizeof(int64_t));
+        }
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < N; ++i) {
+            row_neighbours(o, i, la, lb, na_, nb_);
+            det_t di = det_of(o, i);
+            int64_t e = ptr[i];
+            for (int lA = 0; lA <= 2; ++lA)
+                for (int lB = 0; lA + lB <= 2; ++lB)
+                    for (int64_t a = 0; a < na_[lA]; ++a)
+                        for (int64_t b = 0; b < nb_[lB]; ++b) {
+                            int64_t j = la[lA][a] * o->nB + lb[lB][b];
+                            cols[e] = j;
+                            vals[e] = slater_condon(o, di, det_of(o, j));
+                            ++e;
+                        }
+        }
+        for (int l = 0; l < 3; ++l) {
+            free(la[l]);
+            free(lb[l]);
+        }
+    }
+}
+
 void oracle_sigma(void *p, const double *x, int nvec, double *out)
 {
     oracle_t *o = (oracle_t *)p;
@@ -623,12 +698,30 @@ int oracle_davidson(void *p, int nroots, double tol, int max_iter, int max_sub, 
             converged = 1;
             break;
         }
-        /* 2h. restart when the subspace would overflow: keep the Ritz vectors */
+        /* 2h. thick restart when the subspace would overflow: keep the lowest
+         * nkeep Ritz vectors V Y[:, :nkeep] and their images W Y[:, :nkeep] */
         int nnew = nroots - nconv;
         if (k + nnew > max_sub) {
-            memcpy(V, U, (size_t)nroots * N * sizeof(double));
-            memcpy(W, HU, (size_t)nroots * N * sizeof(double));
-            k = nroots;
+            int nkeep = max_sub / 3;
+            if (nkeep < 2 * nroots) nkeep = 2 * nroots;
+            if (nkeep > max_sub - nroots) nkeep = max_sub - nroots;
+            if (nkeep < nroots) nkeep = nroots;
+            if (nkeep > k) nkeep = k;
+            double *V2 = (double *)calloc((size_t)nkeep * N, sizeof(double));
+            double *W2 = (double *)calloc((size_t)nkeep * N, sizeof(double));
+            for (int c = 0; c < nkeep; ++c)
+                for (int a = 0; a < k; ++a) {
+                    double y = Y[a * k + c];
+                    for (int64_t i = 0; i < N; ++i) {
+                        V2[(size_t)c * N + i] += y * V[(size_t)a * N + i];
+                        W2[(size_t)c * N + i] += y * W[(size_t)a * N + i];
+                    }
+                }
+            memcpy(V, V2, (size_t)nkeep * N * sizeof(double));
+            memcpy(W, W2, (size_t)nkeep * N * sizeof(double));
+            free(V2);
+            free(W2);
+            k = nkeep;
         }
         /* 2f-2g. precondition each unconverged residual, orthogonalise, append */
         int added = 0;

@@ -1,0 +1,153 @@
+// Internal declarations of the SBD CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "sbd.h"
+
+namespace sbd {
+
+// ---------------------------------------------------------------------------
+// errors: thrown inside the library, converted to status codes at the ABI
+
+struct Error {
+    int code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string &msg);
+void check_cuda(cudaError_t e, const char *what, const char *file, int line);
+void count_launch();
+#define SBD_CUDA(call) ::sbd::check_cuda((call), #call, __FILE__, __LINE__)
+#define SBD_LAUNCH(what) (::sbd::count_launch(), ::sbd::check_cuda(cudaGetLastError(), what, __FILE__, __LINE__))
+
+// ---------------------------------------------------------------------------
+// device status words written by validation kernels
+
+struct DevStatus {
+    unsigned long long first_bad;  // smallest index of a malformed string (~0 if none)
+    unsigned long long first_dup;  // smallest index i with sorted[i] == sorted[i-1]
+    int nonfinite;                 // nonzero if h or eri hold NaN/Inf
+    int differ;                    // nonzero if two sorted sets differ
+};
+
+// ---------------------------------------------------------------------------
+// per-spin tables, all device memory
+
+struct SpinTables {
+    int nel = 0;                 // electrons of this spin
+    int64_t n = 0;               // |S|
+    uint64_t *strings = nullptr; // sorted ascending
+    // canonical CSR excitation tables (kind 1 singles, kind 2 doubles)
+    int64_t *s_ptr = nullptr, *d_ptr = nullptr;  // [n+1]
+    int64_t ns = 0, nd = 0;                      // total entries
+    int32_t *s_j = nullptr, *d_j = nullptr;      // target index
+    uint8_t *s_orb = nullptr, *d_orb = nullptr;  // p1,p2,q1,q2 per entry
+    int8_t *s_sign = nullptr, *d_sign = nullptr; // fermionic phase
+    int32_t *s_code = nullptr;  // p*norb+q of a single, bit 31 set when the phase is -1
+    double *s_v64 = nullptr, *d_v64 = nullptr;   // same-spin matrix elements
+    float *s_v32 = nullptr, *d_v32 = nullptr;
+    double *ediag = nullptr;     // [n] same-spin diagonal energies
+    int max_singles = 0;         // longest singles list
+    bool alias = false;          // storage owned by the other spin (A == B)
+};
+
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    sbd_options opt{};
+    int norb = 0, na = 0, nb = 0;
+    int64_t nA = 0, nB = 0, N = 0;
+    double *h64 = nullptr, *eri64 = nullptr;
+    float *eri32 = nullptr;
+    SpinTables sp[2];
+    double *hd = nullptr;   // [N] Hamiltonian diagonal
+    void *work_t = nullptr; // [N] doubles: transposed copy of one vector
+    size_t bytes_held = 0;
+    std::vector<std::pair<void *, size_t>> allocs;
+    std::string last_error;
+    DevStatus *dstat = nullptr;  // device
+    int smem_optin = 0;          // max dynamic shared memory per block
+    int num_sms = 0;
+    // kernel timing (sbd_options.timing)
+    struct Pending {
+        int slot;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double kernel_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t kernel_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+// kernel timing helpers (api.cu)
+cudaEvent_t take_event(Ctx &c);
+void harvest_timing(Ctx &c);
+
+// device memory through the handle's allocator, with budget accounting
+void *dalloc(Ctx &c, size_t bytes);
+void dfree(Ctx &c, void *p);
+template <typename T>
+T *dalloc_n(Ctx &c, size_t n)
+{
+    return static_cast<T *>(dalloc(c, n * sizeof(T) > 0 ? n * sizeof(T) : 16));
+}
+
+// ---------------------------------------------------------------------------
+// warp-cooperative search, shared by the lookup entry point and the table builder
+
+// Position of `key` in sorted[0, n), or -1.  All 32 lanes call it with the
+// same key; each step samples 32 evenly spaced elements of the remaining
+// range and narrows it to one gap between samples (a 32-ary search).
+__device__ __forceinline__ int64_t warp_find(const uint64_t *__restrict__ sorted, int64_t n, uint64_t key)
+{
+    const int lane = threadIdx.x & 31;
+    int64_t lo = 0, hi = n;  // first element >= key lies in [lo, hi]
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t pos = lo + lane * step;
+        const bool below = pos < hi && __ldg(sorted + pos) < key;
+        const int c = __popc(__ballot_sync(0xffffffffu, below));
+        const int64_t nlo = c == 0 ? lo : lo + (int64_t)(c - 1) * step + 1;
+        const int64_t nhi = min(hi, lo + (int64_t)c * step + 1);
+        lo = nlo;
+        hi = nhi;
+    }
+    const int64_t pos = lo + lane;
+    const bool hit = pos < hi && pos < n && __ldg(sorted + pos) == key;
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    return m ? lo + (__ffs(m) - 1) : -1;
+}
+
+// ---------------------------------------------------------------------------
+// launchers (each enqueues on c.stream unless a stream is given)
+
+// strings.cu
+void validate_strings(Ctx &c, const uint64_t *s, int64_t n, int norb, int nel);
+void radix_sort_strings(Ctx &c, uint64_t *keys, int64_t n, int nbits);
+void check_duplicates(Ctx &c, const uint64_t *sorted, int64_t n);
+void compare_sets(Ctx &c, const uint64_t *a, const uint64_t *b, int64_t n);
+void check_finite(Ctx &c, const double *x, int64_t n);
+void lookup_strings(const uint64_t *sorted, int64_t n, const uint64_t *keys, int64_t nq, int64_t *idx,
+                    cudaStream_t s);
+
+// tables.cu
+void build_tables(Ctx &c, int spin);
+void build_diagonal(Ctx &c);
+void to_float(const double *in, float *out, int64_t n, cudaStream_t s);
+
+// sigma.cu
+void sigma_prepare(Ctx &c);
+// c64 (mixed only, may be NULL): the FP64 amplitudes, used for the diagonal term
+void sigma_apply(Ctx &c, const void *cvec, double *svec, sbd_precision prec, cudaStream_t s,
+                 const double *c64 = nullptr);
+
+// davidson.cu
+int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energies, double *vecs,
+             double *resid, sbd_report *rep);
+
+}  // namespace sbd

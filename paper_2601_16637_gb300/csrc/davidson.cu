@@ -1,0 +1,716 @@
+// Block Davidson on the device (paper Sec. II-C, with the damped diagonal
+// preconditioner of Sec. II-E and the stopping tests of Sec. II-G).
+//
+// Per iteration: Rayleigh-Ritz on the projected matrix T = V^T W (cyclic
+// Jacobi in one CTA), Ritz vectors U = V Y and HU = W Y with residual norms,
+// the preconditioned corrections t = r / (sign(d) max(|d|, delta)),
+// d = Hd - theta, block classical Gram-Schmidt with one re-orthogonalisation
+// pass against the basis, and the sigma product of the new basis vectors.
+// A thick restart keeps the lowest Ritz vectors when the basis is full.
+//
+// All vectors, T, the Ritz quantities and every reduction are FP64 (two-stage
+// reductions in a fixed order, so results are reproducible).  In mixed mode
+// the sigma of new basis vectors uses FP32 amplitudes (SBD_MIXED); when the
+// residual computed from that sigma stops improving, the Ritz vectors are
+// multiplied by the FP64 sigma (defect correction): their FP64 Rayleigh
+// quotients and residuals decide convergence, and the basis restarts from
+// them with exact W columns.  Only converged FP64-evaluated residuals end
+// the solve.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <chrono>
+
+#include "common.cuh"
+
+namespace sbd {
+
+namespace {
+
+constexpr int kBlas = 256;      // threads per BLAS block
+constexpr int kDotBatch = 16;   // vectors per multi-dot launch
+constexpr int kMaxSub = 64;     // largest subspace the Jacobi kernel takes
+
+int blas_grid(const Ctx &c, int64_t N)
+{
+    int64_t g = (N + kBlas - 1) / kBlas;
+    int64_t cap = (int64_t)4 * (c.num_sms > 0 ? c.num_sms : 152);
+    return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *red)
+{
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    T s = T(0);
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    return s;  // valid in thread 0
+}
+
+// partial[b*kDotBatch + a] = sum over block b's elements of X[a][i] * y[i], a < k <= kDotBatch
+__global__ void __launch_bounds__(kBlas) mdot_partial(const double *__restrict__ X, int64_t ldx, int k,
+                                                      const double *__restrict__ y, int64_t N, double *partial)
+{
+    __shared__ double red[kBlas / 32];
+    double acc[kDotBatch];
+#pragma unroll
+    for (int a = 0; a < kDotBatch; ++a) acc[a] = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kBlas + threadIdx.x; i < N; i += (int64_t)gridDim.x * kBlas) {
+        const double yi = y[i];
+#pragma unroll
+        for (int a = 0; a < kDotBatch; ++a)
+            if (a < k) acc[a] += X[a * ldx + i] * yi;
+    }
+    for (int a = 0; a < k; ++a) {
+        const double s = block_sum(acc[a], red);
+        if (threadIdx.x == 0) partial[blockIdx.x * kDotBatch + a] = s;
+    }
+}
+
+// out1[a*st1] (and out2[a*st2] when given) = sum_b partial[b][a], fixed order
+__global__ void mdot_final(const double *partial, int nblocks, int k, double *out1, int64_t st1, double *out2,
+                           int64_t st2)
+{
+    const int a = threadIdx.x;
+    if (a >= k) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partial[b * kDotBatch + a];
+    out1[a * st1] = s;
+    if (out2) out2[a * st2] = s;
+}
+
+// y -= sum_a coef[a] X[a], a < k <= kDotBatch
+__global__ void __launch_bounds__(kBlas) maxpy_kernel(const double *__restrict__ X, int64_t ldx, int k,
+                                                      const double *__restrict__ coef, double *y, int64_t N)
+{
+    double c[kDotBatch];
+#pragma unroll
+    for (int a = 0; a < kDotBatch; ++a) c[a] = a < k ? coef[a] : 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kBlas + threadIdx.x; i < N; i += (int64_t)gridDim.x * kBlas) {
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < kDotBatch; ++a)
+            if (a < k) s += c[a] * X[a * ldx + i];
+        y[i] -= s;
+    }
+}
+
+// out[j] = sum_a Y[a*ldy + j] X[a] for j < m <= kDotBatch, a < k
+__global__ void __launch_bounds__(kBlas) combine_kernel(const double *__restrict__ X, int64_t ldx, int k,
+                                                        const double *__restrict__ Y, int ldy, int m, double *out,
+                                                        int64_t ldo, int64_t N)
+{
+    __shared__ double ys[kMaxSub * kDotBatch];
+    for (int t = threadIdx.x; t < k * m; t += kBlas) ys[t] = Y[(t / m) * ldy + (t % m)];
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)kBlas + threadIdx.x; i < N; i += (int64_t)gridDim.x * kBlas) {
+        double acc[kDotBatch];
+#pragma unroll
+        for (int j = 0; j < kDotBatch; ++j) acc[j] = 0.0;
+        for (int a = 0; a < k; ++a) {
+            const double x = X[a * ldx + i];
+#pragma unroll
+            for (int j = 0; j < kDotBatch; ++j)
+                if (j < m) acc[j] += ys[a * m + j] * x;
+        }
+#pragma unroll
+        for (int j = 0; j < kDotBatch; ++j)
+            if (j < m) out[j * ldo + i] = acc[j];
+    }
+}
+
+// partial[b*kDotBatch + j] = sum over block b of (HU[j] - theta[j] U[j])^2
+__global__ void __launch_bounds__(kBlas) resid_partial(const double *__restrict__ U, const double *__restrict__ HU,
+                                                       int64_t ld, int m, const double *__restrict__ theta,
+                                                       int64_t N, double *partial)
+{
+    __shared__ double red[kBlas / 32];
+    double acc[kDotBatch];
+#pragma unroll
+    for (int j = 0; j < kDotBatch; ++j) acc[j] = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kBlas + threadIdx.x; i < N; i += (int64_t)gridDim.x * kBlas) {
+#pragma unroll
+        for (int j = 0; j < kDotBatch; ++j)
+            if (j < m) {
+                const double r = HU[j * ld + i] - theta[j] * U[j * ld + i];
+                acc[j] += r * r;
+            }
+    }
+    for (int j = 0; j < m; ++j) {
+        const double s = block_sum(acc[j], red);
+        if (threadIdx.x == 0) partial[blockIdx.x * kDotBatch + j] = s;
+    }
+}
+
+// t = (hu - theta u) / (sign(d) max(|d|, delta)), d = Hd - theta   (Eq. 7)
+__global__ void precond_kernel(const double *__restrict__ u, const double *__restrict__ hu,
+                               const double *__restrict__ hd, const double *__restrict__ theta, double delta,
+                               double *t, int64_t N)
+{
+    const double th = *theta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = hd[i] - th;
+        const double den = (d >= 0.0 ? 1.0 : -1.0) * fmax(fabs(d), delta);
+        t[i] = (hu[i] - th * u[i]) / den;
+    }
+}
+
+__global__ void scale_kernel(double *x, double s, int64_t N)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] *= s;
+}
+
+__global__ void set_kernel(double *x, int64_t idx, double v) { x[idx] = v; }
+
+// two-stage argmin of x over indices not in excl[0..nexcl); ties -> lower index
+__global__ void argmin_partial(const double *__restrict__ x, int64_t N, const int64_t *excl, int nexcl,
+                               double *pv, int64_t *pi)
+{
+    __shared__ double sv[kBlas];
+    __shared__ int64_t si[kBlas];
+    double bv = INFINITY;
+    int64_t bi = -1;
+    for (int64_t i = blockIdx.x * (int64_t)kBlas + threadIdx.x; i < N; i += (int64_t)gridDim.x * kBlas) {
+        bool skip = false;
+        for (int e = 0; e < nexcl; ++e) skip |= excl[e] == i;
+        if (skip) continue;
+        const double v = x[i];
+        if (bi < 0 || v < bv || (v == bv && i < bi)) {
+            bv = v;
+            bi = i;
+        }
+    }
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = kBlas / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            const double ov = sv[threadIdx.x + s];
+            const int64_t oi = si[threadIdx.x + s];
+            if (oi >= 0 && (si[threadIdx.x] < 0 || ov < sv[threadIdx.x] || (ov == sv[threadIdx.x] && oi < si[threadIdx.x]))) {
+                sv[threadIdx.x] = ov;
+                si[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        pv[blockIdx.x] = sv[0];
+        pi[blockIdx.x] = si[0];
+    }
+}
+
+// index of the largest |x_i| (ties -> lower index) in pi[blockIdx]
+__global__ void argmaxabs_partial(const double *__restrict__ x, int64_t N, double *pv, int64_t *pi)
+{
+    __shared__ double sv[kBlas];
+    __shared__ int64_t si[kBlas];
+    double bv = -1.0;
+    int64_t bi = -1;
+    for (int64_t i = blockIdx.x * (int64_t)kBlas + threadIdx.x; i < N; i += (int64_t)gridDim.x * kBlas) {
+        const double v = fabs(x[i]);
+        if (v > bv) {
+            bv = v;
+            bi = i;
+        }
+    }
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = kBlas / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            const double ov = sv[threadIdx.x + s];
+            const int64_t oi = si[threadIdx.x + s];
+            if (oi >= 0 && (ov > sv[threadIdx.x] || (ov == sv[threadIdx.x] && oi < si[threadIdx.x]))) {
+                sv[threadIdx.x] = ov;
+                si[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        pv[blockIdx.x] = sv[0];
+        pi[blockIdx.x] = si[0];
+    }
+}
+
+// Eigenpairs of the symmetric k x k matrix T (upper and lower parts averaged)
+// by cyclic Jacobi rotations in one CTA.  evals ascending; Y[a*ldy + j] is
+// component a of eigenvector j.
+__global__ void jacobi_kernel(const double *__restrict__ T, int ldt, int k, double *evals, double *Y, int ldy)
+{
+    extern __shared__ double js[];
+    double *A = js, *V = js + k * k;
+    __shared__ double rot[2];
+    __shared__ int flag;
+    __shared__ double red[32];
+    __shared__ int ord[kMaxSub];
+    const int tid = threadIdx.x;
+    for (int t = tid; t < k * k; t += blockDim.x) {
+        const int i = t / k, j = t % k;
+        A[t] = 0.5 * (T[i * ldt + j] + T[j * ldt + i]);
+        V[t] = i == j ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    double fro = 0.0;
+    for (int t = tid; t < k * k; t += blockDim.x) fro += A[t] * A[t];
+    fro = block_sum(fro, red);
+    __shared__ double fro_s;
+    if (tid == 0) fro_s = sqrt(fro) > 0.0 ? sqrt(fro) : 1.0;
+    __syncthreads();
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int t = tid; t < k * k; t += blockDim.x) {
+            const int i = t / k, j = t % k;
+            if (i < j) off += A[t] * A[t];
+        }
+        off = block_sum(off, red);
+        if (tid == 0) flag = sqrt(off) <= 1e-17 * fro_s;
+        __syncthreads();
+        if (flag) break;
+        for (int p = 0; p < k - 1; ++p)
+            for (int q = p + 1; q < k; ++q) {
+                if (tid == 0) {
+                    const double apq = A[p * k + q];
+                    flag = apq == 0.0;
+                    if (!flag) {
+                        const double theta = (A[q * k + q] - A[p * k + p]) / (2.0 * apq);
+                        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        const double c = 1.0 / sqrt(t * t + 1.0);
+                        rot[0] = c;
+                        rot[1] = t * c;
+                    }
+                }
+                __syncthreads();
+                if (flag) {
+                    __syncthreads();
+                    continue;
+                }
+                const double c = rot[0], s = rot[1];
+                if (tid < k) {
+                    const int r = tid;
+                    const double arp = A[r * k + p], arq = A[r * k + q];
+                    A[r * k + p] = c * arp - s * arq;
+                    A[r * k + q] = s * arp + c * arq;
+                }
+                __syncthreads();
+                if (tid < k) {
+                    const int r = tid;
+                    const double apr = A[p * k + r], aqr = A[q * k + r];
+                    A[p * k + r] = c * apr - s * aqr;
+                    A[q * k + r] = s * apr + c * aqr;
+                    const double vrp = V[r * k + p], vrq = V[r * k + q];
+                    V[r * k + p] = c * vrp - s * vrq;
+                    V[r * k + q] = s * vrp + c * vrq;
+                }
+                __syncthreads();
+            }
+    }
+    if (tid == 0) {
+        for (int i = 0; i < k; ++i) ord[i] = i;
+        for (int i = 0; i < k; ++i)
+            for (int j = i + 1; j < k; ++j)
+                if (A[ord[j] * k + ord[j]] < A[ord[i] * k + ord[i]]) {
+                    const int t = ord[i];
+                    ord[i] = ord[j];
+                    ord[j] = t;
+                }
+    }
+    __syncthreads();
+    for (int t = tid; t < k * k; t += blockDim.x) {
+        const int a = t / k, j = t % k;
+        Y[a * ldy + j] = V[a * k + ord[j]];
+    }
+    for (int j = tid; j < k; j += blockDim.x) evals[j] = A[ord[j] * k + ord[j]];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
+struct Work {
+    Ctx &c;
+    cudaStream_t s;
+    int64_t N;
+    int grid;
+    double *partial = nullptr;  // [grid][kDotBatch]
+    double *pv = nullptr;
+    int64_t *pi = nullptr;
+    std::vector<double> hpart;
+    explicit Work(Ctx &cc) : c(cc), s(cc.stream), N(cc.N), grid(blas_grid(cc, cc.N)) {}
+
+    // out[a] (device, stride st) = X[a] . y, a < k
+    void dots(const double *X, int64_t ldx, int k, const double *y, double *out1, int64_t st1,
+              double *out2 = nullptr, int64_t st2 = 0)
+    {
+        for (int a0 = 0; a0 < k; a0 += kDotBatch) {
+            const int kb = std::min(kDotBatch, k - a0);
+            mdot_partial<<<grid, kBlas, 0, s>>>(X + a0 * ldx, ldx, kb, y, N, partial);
+            SBD_LAUNCH("mdot_partial");
+            mdot_final<<<1, kDotBatch, 0, s>>>(partial, grid, kb, out1 + a0 * st1, st1,
+                                               out2 ? out2 + a0 * st2 : nullptr, st2);
+            SBD_LAUNCH("mdot_final");
+        }
+    }
+    void axpys(const double *X, int64_t ldx, int k, const double *coef, double *y)
+    {
+        for (int a0 = 0; a0 < k; a0 += kDotBatch) {
+            const int kb = std::min(kDotBatch, k - a0);
+            maxpy_kernel<<<grid, kBlas, 0, s>>>(X + a0 * ldx, ldx, kb, coef + a0, y, N);
+            SBD_LAUNCH("maxpy_kernel");
+        }
+    }
+    // out[j] = sum_a Y[a][j] X[a], j < m, a < k
+    void combine(const double *X, int64_t ldx, int k, const double *Y, int ldy, int m, double *out, int64_t ldo)
+    {
+        for (int j0 = 0; j0 < m; j0 += kDotBatch) {
+            const int mb = std::min(kDotBatch, m - j0);
+            combine_kernel<<<grid, kBlas, 0, s>>>(X, ldx, k, Y + j0, ldy, mb, out + j0 * ldo, ldo, N);
+            SBD_LAUNCH("combine_kernel");
+        }
+    }
+    double norm(const double *x, double *dscratch)
+    {
+        dots(x, 0, 1, x, dscratch, 1);
+        double v = 0.0;
+        SBD_CUDA(cudaMemcpyAsync(&v, dscratch, sizeof(double), cudaMemcpyDeviceToHost, s));
+        SBD_CUDA(cudaStreamSynchronize(s));
+        return sqrt(v);
+    }
+    void scale(double *x, double f)
+    {
+        scale_kernel<<<grid, kBlas, 0, s>>>(x, f, N);
+        SBD_LAUNCH("scale_kernel");
+    }
+    // residual norms ||HU_j - theta_j U_j||, j < m (theta on device)
+    void resid_norms(const double *U, const double *HU, int64_t ld, int m, const double *theta, double *out_host)
+    {
+        hpart.assign((size_t)grid * kDotBatch, 0.0);
+        for (int j0 = 0; j0 < m; j0 += kDotBatch) {
+            const int mb = std::min(kDotBatch, m - j0);
+            resid_partial<<<grid, kBlas, 0, s>>>(U + j0 * ld, HU + j0 * ld, ld, mb, theta + j0, N, partial);
+            SBD_LAUNCH("resid_partial");
+            SBD_CUDA(cudaMemcpyAsync(hpart.data(), partial, sizeof(double) * grid * kDotBatch,
+                                     cudaMemcpyDeviceToHost, s));
+            SBD_CUDA(cudaStreamSynchronize(s));
+            for (int j = 0; j < mb; ++j) {
+                double acc = 0.0;
+                for (int b = 0; b < grid; ++b) acc += hpart[(size_t)b * kDotBatch + j];
+                out_host[j0 + j] = sqrt(acc);
+            }
+        }
+    }
+    int64_t argmin(const double *x, const std::vector<int64_t> &excl, int64_t *dexcl)
+    {
+        if (!excl.empty())
+            SBD_CUDA(cudaMemcpyAsync(dexcl, excl.data(), excl.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        argmin_partial<<<grid, kBlas, 0, s>>>(x, N, dexcl, (int)excl.size(), pv, pi);
+        SBD_LAUNCH("argmin_partial");
+        std::vector<double> v(grid);
+        std::vector<int64_t> id(grid);
+        SBD_CUDA(cudaMemcpyAsync(v.data(), pv, sizeof(double) * grid, cudaMemcpyDeviceToHost, s));
+        SBD_CUDA(cudaMemcpyAsync(id.data(), pi, sizeof(int64_t) * grid, cudaMemcpyDeviceToHost, s));
+        SBD_CUDA(cudaStreamSynchronize(s));
+        int64_t bi = -1;
+        double bv = INFINITY;
+        for (int b = 0; b < grid; ++b)
+            if (id[b] >= 0 && (bi < 0 || v[b] < bv || (v[b] == bv && id[b] < bi))) {
+                bv = v[b];
+                bi = id[b];
+            }
+        return bi;
+    }
+    double value_at_argmaxabs(const double *x)
+    {
+        argmaxabs_partial<<<grid, kBlas, 0, s>>>(x, N, pv, pi);
+        SBD_LAUNCH("argmaxabs_partial");
+        std::vector<double> v(grid);
+        std::vector<int64_t> id(grid);
+        SBD_CUDA(cudaMemcpyAsync(v.data(), pv, sizeof(double) * grid, cudaMemcpyDeviceToHost, s));
+        SBD_CUDA(cudaMemcpyAsync(id.data(), pi, sizeof(int64_t) * grid, cudaMemcpyDeviceToHost, s));
+        SBD_CUDA(cudaStreamSynchronize(s));
+        int64_t bi = -1;
+        double bv = -1.0;
+        for (int b = 0; b < grid; ++b)
+            if (id[b] >= 0 && (v[b] > bv || (v[b] == bv && id[b] < bi))) {
+                bv = v[b];
+                bi = id[b];
+            }
+        double val = 0.0;
+        SBD_CUDA(cudaMemcpyAsync(&val, x + bi, sizeof(double), cudaMemcpyDeviceToHost, s));
+        SBD_CUDA(cudaStreamSynchronize(s));
+        return val;
+    }
+};
+
+}  // namespace
+
+int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energies, double *vecs, double *resid,
+             sbd_report *rep)
+{
+    using clock = std::chrono::steady_clock;
+    const auto t_start = clock::now();
+    const int64_t N = c.N;
+    if (nroots < 1 || nroots > kDotBatch || nroots > N) fail(SBD_ERR_INVALID_ARG, "nroots must be in 1..min(16, N)");
+    if (!(tol > 0.0)) fail(SBD_ERR_INVALID_ARG, "tol must be positive");
+    const double delta = c.opt.delta > 0.0 ? c.opt.delta : 1e-4;
+    const int max_iter = c.opt.max_iter > 0 ? c.opt.max_iter : 200;
+    int max_sub = c.opt.max_subspace > 0 ? c.opt.max_subspace : std::max(24, 8 * nroots);
+    max_sub = std::min<int64_t>(std::min(max_sub, kMaxSub), N);
+    if (max_sub < 2 * nroots && N >= 2 * nroots) max_sub = 2 * nroots;
+    const bool mixed = prec == SBD_MIXED;
+
+    // keep the basis inside the budget: V, W, U, HU, t (+ FP32 copy)
+    auto need = [&](int ms, int nk) {
+        return ((size_t)(2 * ms + 2 * nk + 1)) * (size_t)N * sizeof(double) + (mixed ? (size_t)N * 4 : 0) + (1u << 22);
+    };
+    int nkeep = std::max(nroots, std::min(max_sub - nroots, std::max(2 * nroots, max_sub / 3)));
+    if (c.opt.hbm_budget_bytes) {
+        while (max_sub > 2 * nroots && c.bytes_held + need(max_sub, nkeep) > c.opt.hbm_budget_bytes) {
+            --max_sub;
+            nkeep = std::max(nroots, std::min(max_sub - nroots, std::max(2 * nroots, max_sub / 3)));
+        }
+    }
+    sbd_report r{};
+    r.status = SBD_OK;
+    SBD_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(2 * sizeof(double) * kMaxSub * kMaxSub)));
+
+    Work w(c);
+    std::vector<void *> owned;
+    auto grab = [&](size_t bytes) {
+        void *p = dalloc(c, bytes);
+        owned.push_back(p);
+        return p;
+    };
+    int status = SBD_OK;
+    try {
+        double *V = (double *)grab((size_t)max_sub * N * sizeof(double));
+        double *W = (double *)grab((size_t)max_sub * N * sizeof(double));
+        double *U = (double *)grab((size_t)nkeep * N * sizeof(double));
+        double *HU = (double *)grab((size_t)nkeep * N * sizeof(double));
+        float *c32 = mixed ? (float *)grab((size_t)N * sizeof(float)) : nullptr;
+        double *T = (double *)grab(sizeof(double) * kMaxSub * kMaxSub);
+        double *Y = (double *)grab(sizeof(double) * kMaxSub * kMaxSub);
+        double *theta = (double *)grab(sizeof(double) * kMaxSub);
+        double *coef = (double *)grab(sizeof(double) * kMaxSub);
+        double *dscr = (double *)grab(sizeof(double) * kMaxSub);
+        int64_t *dexcl = (int64_t *)grab(sizeof(int64_t) * (kDotBatch + 1));
+        w.partial = (double *)grab(sizeof(double) * (size_t)w.grid * kDotBatch);
+        w.pv = (double *)grab(sizeof(double) * w.grid);
+        w.pi = (int64_t *)grab(sizeof(int64_t) * w.grid);
+        const int64_t ld = N;
+        cudaEvent_t ev0, ev1;
+        SBD_CUDA(cudaEventCreate(&ev0));
+        SBD_CUDA(cudaEventCreate(&ev1));
+        double sigma_ms = 0.0;
+
+        // exact[a]: W column a came from the FP64 sigma (always, in FP64 mode)
+        std::vector<char> exact(kMaxSub, mixed ? 0 : 1);
+        auto sigma_cols = [&](int b0, int nb, bool fp64) {
+            SBD_CUDA(cudaEventRecord(ev0, w.s));
+            for (int b = b0; b < b0 + nb; ++b) {
+                if (!fp64) {
+                    to_float(V + b * ld, c32, N, w.s);
+                    sigma_apply(c, c32, W + b * ld, SBD_MIXED, w.s, V + b * ld);
+                    r.sigma_mixed++;
+                } else {
+                    sigma_apply(c, V + b * ld, W + b * ld, SBD_FP64, w.s);
+                    r.sigma_fp64++;
+                }
+                exact[b] = fp64;
+            }
+            SBD_CUDA(cudaEventRecord(ev1, w.s));
+            SBD_CUDA(cudaEventSynchronize(ev1));
+            float ms = 0.f;
+            SBD_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+            sigma_ms += ms;
+        };
+        // column b of T (and its mirror row) against V[0..kk): T[a][b] = V[a].W[b].  Where one of
+        // the pair has an FP64-exact W column and the other does not, the exact one is used,
+        // T[a][b] = W[a].V[b], so that mixed-precision noise never couples into exact columns.
+        auto extend_T = [&](int b, int kk) {
+            w.dots(V, ld, kk, W + b * ld, T + b, kMaxSub, T + b * kMaxSub, 1);
+            if (!exact[b])
+                for (int a = 0; a < kk; ++a)
+                    if (exact[a] && a != b)
+                        w.dots(W + a * ld, 0, 1, V + b * ld, T + a * kMaxSub + b, 1, T + b * kMaxSub + a, 1);
+        };
+        auto rebuild_T = [&](int kk) {
+            SBD_CUDA(cudaMemsetAsync(T, 0, sizeof(double) * kMaxSub * kMaxSub, w.s));
+            for (int b = 0; b < kk; ++b)
+                if (!exact[b]) extend_T(b, kk);
+            for (int b = 0; b < kk; ++b)
+                if (exact[b]) w.dots(V, ld, kk, W + b * ld, T + b, kMaxSub, T + b * kMaxSub, 1);
+        };
+        // V' = V Y[:, :nk], W' = W Y[:, :nk] through the U/HU staging buffers
+        auto compress = [&](int kk, int nk) {
+            w.combine(V, ld, kk, Y, kMaxSub, nk, U, ld);
+            w.combine(W, ld, kk, Y, kMaxSub, nk, HU, ld);
+            SBD_CUDA(cudaMemcpyAsync(V, U, (size_t)nk * N * sizeof(double), cudaMemcpyDeviceToDevice, w.s));
+            SBD_CUDA(cudaMemcpyAsync(W, HU, (size_t)nk * N * sizeof(double), cudaMemcpyDeviceToDevice, w.s));
+        };
+
+        // 1. initial vectors: unit vectors on the lowest diagonal entries
+        SBD_CUDA(cudaMemsetAsync(V, 0, (size_t)nroots * N * sizeof(double), w.s));
+        std::vector<int64_t> chosen;
+        for (int j = 0; j < nroots; ++j) {
+            const int64_t idx = w.argmin(c.hd, chosen, dexcl);
+            chosen.push_back(idx);
+            set_kernel<<<1, 1, 0, w.s>>>(V + j * ld, idx, 1.0);
+            SBD_LAUNCH("set_kernel");
+        }
+        int k = nroots;
+        sigma_cols(0, k, !mixed);
+        rebuild_T(k);
+
+        std::vector<double> th(kMaxSub), rn(nroots), hist;
+        bool converged = false;
+        double switch_floor = -1.0;  // mixed: residual level that triggers an FP64 check
+        int since_ref = 0;
+        int iter = 0;
+        while (true) {
+            // 2b-2c. Rayleigh-Ritz
+            jacobi_kernel<<<1, 128, 2 * sizeof(double) * k * k, w.s>>>(T, kMaxSub, k, theta, Y, kMaxSub);
+            SBD_LAUNCH("jacobi_kernel");
+            // 2d. Ritz vectors and residuals
+            w.combine(V, ld, k, Y, kMaxSub, nroots, U, ld);
+            w.combine(W, ld, k, Y, kMaxSub, nroots, HU, ld);
+            w.resid_norms(U, HU, ld, nroots, theta, rn.data());
+            SBD_CUDA(cudaMemcpyAsync(th.data(), theta, sizeof(double) * k, cudaMemcpyDeviceToHost, w.s));
+            SBD_CUDA(cudaStreamSynchronize(w.s));
+            harvest_timing(c);
+            double rmax = *std::max_element(rn.begin(), rn.end());
+            if (c.opt.verbose)
+                fprintf(stderr, "[sbd] iter %d k=%d theta0=%.12f rmax=%.3e %s\n", iter, k, th[0] + c.opt.ecore, rmax,
+                        mixed ? "mixed" : "fp64");
+            bool checked = !mixed;
+            if (mixed) {
+                hist.push_back(rmax);
+                ++since_ref;
+                double thmax = 0.0;
+                for (int j = 0; j < nroots; ++j) thmax = std::max(thmax, fabs(th[j]));
+                const double floor_now = switch_floor >= 0.0 ? switch_floor : std::max(tol, 1e-6 * thmax);
+                // no halving in 8 iterations, at a level where FP32 noise can matter
+                const bool stalled = since_ref > 8 && rmax > 0.5 * hist[hist.size() - 9] && rmax < 1e-4 * thmax;
+                if (rmax <= std::max(tol, floor_now) || stalled || iter >= max_iter) {
+                    // defect correction: keep the lowest Ritz vectors, replace the target
+                    // columns' W by the FP64 sigma, judge convergence on FP64 residuals
+                    const int nk = std::min(std::max(nkeep, nroots), k);
+                    compress(k, nk);
+                    sigma_cols(0, nroots, true);
+                    SBD_CUDA(cudaMemcpyAsync(HU, W, (size_t)nroots * N * sizeof(double), cudaMemcpyDeviceToDevice, w.s));
+                    for (int j = 0; j < nroots; ++j) {
+                        w.dots(U + j * ld, 0, 1, HU + j * ld, dscr + 2 * j, 1);
+                        w.dots(U + j * ld, 0, 1, U + j * ld, dscr + 2 * j + 1, 1);
+                    }
+                    std::vector<double> hd2(2 * nroots);
+                    SBD_CUDA(cudaMemcpyAsync(hd2.data(), dscr, sizeof(double) * 2 * nroots, cudaMemcpyDeviceToHost, w.s));
+                    SBD_CUDA(cudaStreamSynchronize(w.s));
+                    for (int j = 0; j < nroots; ++j) th[j] = hd2[2 * j] / hd2[2 * j + 1];
+                    SBD_CUDA(cudaMemcpyAsync(theta, th.data(), sizeof(double) * nroots, cudaMemcpyHostToDevice, w.s));
+                    w.resid_norms(U, HU, ld, nroots, theta, rn.data());
+                    rmax = *std::max_element(rn.begin(), rn.end());
+                    r.refinements++;
+                    checked = true;
+                    if (c.opt.verbose)
+                        fprintf(stderr, "[sbd] refine %d theta0=%.12f rmax(fp64)=%.3e k=%d\n", r.refinements,
+                                th[0] + c.opt.ecore, rmax, nk);
+                    k = nk;
+                    for (int a = nroots; a < k; ++a) exact[a] = 0;
+                    rebuild_T(k);
+                    switch_floor = std::max(0.5 * tol, 1e-3 * rmax);
+                    since_ref = 0;
+                    hist.clear();
+                }
+            }
+            if (checked) {
+                int nconv = 0;
+                for (int j = 0; j < nroots; ++j) nconv += rn[j] <= tol;
+                if (nconv == nroots) {
+                    converged = true;
+                    break;
+                }
+            }
+            if (iter >= max_iter) break;
+            ++iter;
+            // 2h. thick restart when the new vectors would not fit
+            int nnew = 0;
+            for (int j = 0; j < nroots; ++j) nnew += rn[j] > tol;
+            if (k + nnew > max_sub) {
+                const int nk = std::min(nkeep, k);
+                compress(k, nk);
+                k = nk;
+                if (mixed)
+                    for (int a = 0; a < k; ++a) exact[a] = 0;
+                // V' = V Y, W' = W Y with orthonormal Y: the projected matrix is diag(theta)
+                std::vector<double> Td((size_t)kMaxSub * kMaxSub, 0.0);
+                for (int a = 0; a < k; ++a) Td[(size_t)a * kMaxSub + a] = th[a];
+                SBD_CUDA(cudaMemcpyAsync(T, Td.data(), sizeof(double) * Td.size(), cudaMemcpyHostToDevice, w.s));
+                SBD_CUDA(cudaStreamSynchronize(w.s));
+                r.restarts++;
+            }
+            // 2f-2g. corrections: precondition, orthogonalise twice against V, normalise, append
+            const int k_old = k;
+            for (int j = 0; j < nroots; ++j) {
+                if (rn[j] <= tol) continue;
+                double *t = V + k * ld;
+                precond_kernel<<<w.grid, kBlas, 0, w.s>>>(U + j * ld, HU + j * ld, c.hd, theta + j, delta, t, N);
+                SBD_LAUNCH("precond_kernel");
+                const double n0 = w.norm(t, dscr);
+                for (int pass = 0; pass < 2; ++pass) {
+                    w.dots(V, ld, k, t, coef, 1);
+                    w.axpys(V, ld, k, coef, t);
+                }
+                const double n1 = w.norm(t, dscr);
+                if (!(n1 > 1e-10 * n0) || !std::isfinite(n1)) continue;
+                w.scale(t, 1.0 / n1);
+                ++k;
+            }
+            if (k == k_old) {
+                status = SBD_ERR_BREAKDOWN;
+                c.last_error = "Davidson breakdown: no correction survived orthogonalisation";
+                break;
+            }
+            // 2a. sigma of the new basis vectors, then extend T
+            sigma_cols(k_old, k - k_old, !mixed);
+            for (int b = k_old; b < k; ++b) extend_T(b, b + 1);
+        }
+        r.iterations = iter;
+        r.seconds_sigma = sigma_ms * 1e-3;
+        // sign convention: the largest-magnitude component of each vector is positive
+        for (int j = 0; j < nroots; ++j) {
+            const double v = w.value_at_argmaxabs(U + j * ld);
+            if (v < 0.0) w.scale(U + j * ld, -1.0);
+        }
+        double rmax = 0.0;
+        for (int j = 0; j < nroots; ++j) {
+            energies[j] = th[j] + c.opt.ecore;
+            if (resid) resid[j] = rn[j];
+            rmax = std::max(rmax, rn[j]);
+        }
+        r.max_residual = rmax;
+        if (vecs)
+            SBD_CUDA(cudaMemcpyAsync(vecs, U, (size_t)nroots * N * sizeof(double), cudaMemcpyDefault, w.s));
+        SBD_CUDA(cudaStreamSynchronize(w.s));
+        SBD_CUDA(cudaEventDestroy(ev0));
+        SBD_CUDA(cudaEventDestroy(ev1));
+        if (status == SBD_OK && !converged) status = SBD_NOT_CONVERGED;
+    } catch (...) {
+        for (void *p : owned) dfree(c, p);
+        throw;
+    }
+    for (void *p : owned) dfree(c, p);
+    r.status = status;
+    r.seconds_total = std::chrono::duration<double>(clock::now() - t_start).count();
+    if (rep) *rep = r;
+    return status;
+}
+
+}  // namespace sbd

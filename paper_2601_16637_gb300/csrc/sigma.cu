@@ -1,0 +1,490 @@
+// Matrix-free sigma product s = H c on the selected space A x B (paper
+// Sec. II-A/B, Eq. 4; the three task types of Sec. III-B).
+//
+// With E_pq split by spin, H = H_alpha (x) 1 + 1 (x) H_beta + V_ab where
+//   H_alpha(I,J) = <I| sum h_pq E_pq + 1/2 sum (pq|rs)(E_pq E_rs - d_qr E_ps) |J>
+// evaluated by the same-spin Slater-Condon rules between alpha strings, and
+//   V_ab = sum_pqrs (pq|rs) E^alpha_pq E^beta_rs.
+// Because every alpha operator pair commutes with the beta creators, the
+// phases factorise: <Ia Ib|E^a_pq E^b_rs|Ja Jb> = <Ia|E_pq|Ja><Ib|E_rs|Jb>.
+// With J_x[uv] = sum_{k in x} (uv|kk) this gives, for output (ia, ib):
+//   s = Hd(ia,ib) c(ia,ib)                                          diagonal
+//     + sum_{jb in doubles(ib)} Hb(ib,jb) c(ia,jb)
+//     + sum_{jb in singles(ib), code rs, phase t} [Hb(ib,jb) + t J_ia[rs]] c(ia,jb)
+//     + sum_{ja in doubles(ia)} Ha(ia,ja) c(ja,ib)
+//     + sum_{ja in singles(ia), code pq, phase u} [Ha(ia,ja) + u J_ib[pq]] c(ja,ib)
+//     + sum_{ja in singles(ia)} sum_{jb in singles(ib)} u t (pq|rs) c(ja,jb)
+// The first three lines are a gather inside row ia of C ("beta pass"), the
+// next two the same gather inside column ib, run on the transpose C^T
+// ("alpha pass", same kernel), and the last line is the alpha-beta pass.
+//
+// Every output element is owned by exactly one thread group in each pass
+// (no atomics), so the result is deterministic.  Rows of C are staged in
+// shared memory, R rows interleaved per column so that one vector load
+// fetches the same column of all R rows; the inner gathers then hit shared
+// memory only.  Precision T = double (FP64) or float (mixed: FP32
+// amplitudes, integrals, products and per-list sums; each list sum and the
+// diagonal term are accumulated into the FP64 output).
+#include "common.cuh"
+
+namespace sbd {
+
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kGroup = 8;  // lanes cooperating on one output column
+constexpr int kGroupsPerWarp = 32 / kGroup;
+constexpr int kCodeMask = 0x7fffffff;
+
+template <typename T, int R>
+struct VecIO;
+template <>
+struct VecIO<float, 4> {
+    __device__ static void ld(const float *p, float (&v)[4])
+    {
+        const float4 x = *reinterpret_cast<const float4 *>(p);
+        v[0] = x.x;
+        v[1] = x.y;
+        v[2] = x.z;
+        v[3] = x.w;
+    }
+    __device__ static void st(float *p, const float (&v)[4])
+    {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <>
+struct VecIO<float, 2> {
+    __device__ static void ld(const float *p, float (&v)[2])
+    {
+        const float2 x = *reinterpret_cast<const float2 *>(p);
+        v[0] = x.x;
+        v[1] = x.y;
+    }
+    __device__ static void st(float *p, const float (&v)[2])
+    {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    }
+};
+template <>
+struct VecIO<double, 2> {
+    __device__ static void ld(const double *p, double (&v)[2])
+    {
+        const double2 x = *reinterpret_cast<const double2 *>(p);
+        v[0] = x.x;
+        v[1] = x.y;
+    }
+    __device__ static void st(double *p, const double (&v)[2])
+    {
+        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    }
+};
+template <typename T>
+struct VecIO<T, 1> {
+    __device__ static void ld(const T *p, T (&v)[1]) { v[0] = *p; }
+    __device__ static void st(T *p, const T (&v)[1]) { *p = v[0]; }
+};
+
+template <int R, typename T>
+__device__ __forceinline__ T pick(const T (&v)[R], int i)
+{
+    T out = v[0];
+#pragma unroll
+    for (int r = 1; r < R; ++r)
+        if (i == r) out = v[r];
+    return out;
+}
+
+__host__ __device__ constexpr size_t round16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+template <typename T>
+struct RowArgs {
+    const T *X;  // [nrow][ncol]
+    int64_t nrow, ncol;
+    double *Y;  // output element (row r, column c) at r*y_rs + c*y_cs
+    int64_t y_rs, y_cs;
+    int accumulate;
+    const double *hd;    // optional diagonal, indexed like Y
+    const double *xd64;  // optional FP64 amplitudes [nrow][ncol] for the diagonal term
+    const uint64_t *row_strings;
+    int norb;
+    const double *eri;  // FP64 integrals, for the J vectors of the staged rows
+    const int64_t *s_ptr;
+    const int32_t *s_j, *s_code;
+    const T *s_v;
+    const int64_t *d_ptr;
+    const int32_t *d_j;
+    const T *d_v;
+};
+
+// Gather pass over rows of X: each CTA stages R consecutive rows, then every
+// output column c sums its excitation list (column spin) inside those rows.
+template <typename T, int R, bool STAGED>
+__global__ void __launch_bounds__(kThreads) row_pass_kernel(const RowArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n2 = a.norb * a.norb;
+    const size_t xs_bytes = STAGED ? round16((size_t)a.ncol * R * sizeof(T)) : 0;
+    T *Xs = reinterpret_cast<T *>(smem);
+    T *Js = reinterpret_cast<T *>(smem + xs_bytes);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gi = lane / kGroup, lig = lane % kGroup;
+    const int64_t ngroups = (kThreads / 32) * kGroupsPerWarp;
+
+    for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < a.nrow; r0 += (int64_t)gridDim.x * R) {
+        const int nr = (int)min((int64_t)R, a.nrow - r0);
+        __syncthreads();
+        if (STAGED) {
+            for (int64_t c = tid; c < a.ncol; c += kThreads) {
+                T v[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[r] = r < nr ? a.X[(r0 + r) * a.ncol + c] : T(0);
+                VecIO<T, R>::st(Xs + c * R, v);
+            }
+        }
+        for (int code = tid; code < n2; code += kThreads) {
+            T v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                double s = 0.0;
+                if (r < nr)
+                    for (uint64_t m = a.row_strings[r0 + r]; m; m &= m - 1ull) {
+                        const int k = __ffsll((long long)m) - 1;
+                        s += __ldg(a.eri + (size_t)code * n2 + (size_t)k * (a.norb + 1));
+                    }
+                v[r] = (T)s;
+            }
+            VecIO<T, R>::st(Js + (size_t)code * R, v);
+        }
+        __syncthreads();
+
+        for (int64_t cb = (int64_t)warp * kGroupsPerWarp; cb < a.ncol; cb += ngroups) {
+            const int64_t c = cb + gi;
+            const bool valid = c < a.ncol;
+            T acc[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = T(0);
+            if (valid) {
+                const int64_t se = a.s_ptr[c + 1];
+                for (int64_t e = a.s_ptr[c] + lig; e < se; e += kGroup) {
+                    const int32_t j = __ldg(a.s_j + e), cd = __ldg(a.s_code + e);
+                    const T v = __ldg(a.s_v + e);
+                    T xj[R], jv[R];
+                    if (STAGED) VecIO<T, R>::ld(Xs + (size_t)j * R, xj);
+                    else xj[0] = a.X[r0 * a.ncol + j];
+                    VecIO<T, R>::ld(Js + (size_t)(cd & kCodeMask) * R, jv);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[r] += (cd < 0 ? v - jv[r] : v + jv[r]) * xj[r];
+                }
+                const int64_t de = a.d_ptr[c + 1];
+                for (int64_t e = a.d_ptr[c] + lig; e < de; e += kGroup) {
+                    const int32_t j = __ldg(a.d_j + e);
+                    const T v = __ldg(a.d_v + e);
+                    T xj[R];
+                    if (STAGED) VecIO<T, R>::ld(Xs + (size_t)j * R, xj);
+                    else xj[0] = a.X[r0 * a.ncol + j];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[r] += v * xj[r];
+                }
+            }
+#pragma unroll
+            for (int off = kGroup / 2; off > 0; off >>= 1)
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], off, kGroup);
+            if (valid && lig < nr) {
+                double out = (double)pick<R>(acc, lig);
+                const int64_t idx = (r0 + lig) * a.y_rs + c * a.y_cs;
+                if (a.hd) {
+                    const double xc = a.xd64 ? a.xd64[(r0 + lig) * a.ncol + c]
+                                             : (double)(STAGED ? Xs[(size_t)c * R + lig] : a.X[(r0 + lig) * a.ncol + c]);
+                    out += a.hd[idx] * xc;
+                }
+                a.Y[idx] = a.accumulate ? a.Y[idx] + out : out;
+            }
+        }
+    }
+}
+
+template <typename T>
+struct AbArgs {
+    const T *C;  // [nA][nB]
+    double *S;   // [nA][nB], accumulated
+    int64_t nA, nB;
+    int norb;
+    const T *eri;  // (pq|rs) as a [norb^2][norb^2] matrix
+    const int64_t *as_ptr;
+    const int32_t *as_j, *as_code;
+    const int64_t *bs_ptr;
+    const int32_t *bs_j, *bs_code;
+};
+
+// Alpha-beta pass: CTA per output row ia.  The alpha single excitations of
+// ia are taken R at a time: their rows C[ja,:] are staged interleaved and
+// W[rs][k] = u_k (p_k q_k|rs) is tabulated; each output column ib then
+// runs over its beta singles (jb, rs, t): acc += t * sum_k W[rs][k] C[ja_k, jb].
+template <typename T, int R, bool STAGED>
+__global__ void __launch_bounds__(kThreads) ab_pass_kernel(const AbArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n2 = a.norb * a.norb;
+    const size_t cs_bytes = STAGED ? round16((size_t)a.nB * R * sizeof(T)) : 0;
+    T *Cs = reinterpret_cast<T *>(smem);
+    T *Ws = reinterpret_cast<T *>(smem + cs_bytes);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gi = lane / kGroup, lig = lane % kGroup;
+    const int64_t ngroups = (kThreads / 32) * kGroupsPerWarp;
+
+    for (int64_t ia = blockIdx.x; ia < a.nA; ia += gridDim.x) {
+        const int64_t e0 = a.as_ptr[ia];
+        const int K = (int)(a.as_ptr[ia + 1] - e0);
+        for (int k0 = 0; k0 < K; k0 += R) {
+            const int kr = min(R, K - k0);
+            int64_t ja[R];
+            int pq[R];
+            T u[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const bool ok = k < kr;
+                ja[k] = ok ? (int64_t)a.as_j[e0 + k0 + k] : 0;
+                const int32_t cd = ok ? a.as_code[e0 + k0 + k] : 0;
+                pq[k] = cd & kCodeMask;
+                u[k] = ok ? (cd < 0 ? T(-1) : T(1)) : T(0);
+            }
+            __syncthreads();
+            if (STAGED) {
+                for (int64_t c = tid; c < a.nB; c += kThreads) {
+                    T v[R];
+#pragma unroll
+                    for (int k = 0; k < R; ++k) v[k] = k < kr ? a.C[ja[k] * a.nB + c] : T(0);
+                    VecIO<T, R>::st(Cs + c * R, v);
+                }
+            }
+            for (int code = tid; code < n2; code += kThreads) {
+                T v[R];
+#pragma unroll
+                for (int k = 0; k < R; ++k) v[k] = u[k] * __ldg(a.eri + (size_t)pq[k] * n2 + code);
+                VecIO<T, R>::st(Ws + (size_t)code * R, v);
+            }
+            __syncthreads();
+
+            for (int64_t cb = (int64_t)warp * kGroupsPerWarp; cb < a.nB; cb += ngroups) {
+                const int64_t ib = cb + gi;
+                const bool valid = ib < a.nB;
+                T acc = T(0);
+                if (valid) {
+                    const int64_t ee = a.bs_ptr[ib + 1];
+                    for (int64_t e = a.bs_ptr[ib] + lig; e < ee; e += kGroup) {
+                        const int32_t jb = __ldg(a.bs_j + e), cd = __ldg(a.bs_code + e);
+                        T cv[R], wv[R];
+                        if (STAGED) VecIO<T, R>::ld(Cs + (size_t)jb * R, cv);
+                        else cv[0] = a.C[ja[0] * a.nB + jb];
+                        VecIO<T, R>::ld(Ws + (size_t)(cd & kCodeMask) * R, wv);
+                        T d = T(0);
+#pragma unroll
+                        for (int k = 0; k < R; ++k) d += wv[k] * cv[k];
+                        acc += cd < 0 ? -d : d;
+                    }
+                }
+#pragma unroll
+                for (int off = kGroup / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off, kGroup);
+                if (valid && lig == 0) {
+                    double *s = a.S + ia * a.nB + ib;
+                    *s += (double)acc;
+                }
+            }
+        }
+    }
+}
+
+// out[c][r] = in[r][c]
+template <typename T>
+__global__ void transpose_kernel(const T *__restrict__ in, T *__restrict__ out, int64_t rows, int64_t cols)
+{
+    __shared__ T tile[32][33];
+    const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += 8) {
+        const int64_t r = by + j, c = bx + threadIdx.x;
+        if (r < rows && c < cols) tile[j][threadIdx.x] = in[r * cols + c];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += 8) {
+        const int64_t c = bx + j, r = by + threadIdx.x;
+        if (r < rows && c < cols) out[c * rows + r] = tile[threadIdx.x][j];
+    }
+}
+
+struct PassCfg {
+    int R = 1;
+    bool staged = false;
+    size_t smem = 0;
+};
+
+PassCfg choose(int64_t ncol, int n2, size_t elem, int rmax, size_t limit)
+{
+    PassCfg p;
+    for (int R = rmax; R >= 1; R /= 2) {
+        size_t b = round16((size_t)ncol * R * elem) + (size_t)n2 * R * elem;
+        if (b <= limit) {
+            p.R = R;
+            p.staged = true;
+            p.smem = b;
+            return p;
+        }
+    }
+    p.R = 1;
+    p.staged = false;
+    p.smem = (size_t)n2 * elem;
+    return p;
+}
+
+size_t smem_limit(const Ctx &c) { return (size_t)c.smem_optin - 1024; }
+
+template <typename T>
+void set_attrs(int optin)
+{
+    if constexpr (sizeof(T) == 4) {
+        SBD_CUDA(cudaFuncSetAttribute(row_pass_kernel<T, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        SBD_CUDA(cudaFuncSetAttribute(ab_pass_kernel<T, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    }
+    SBD_CUDA(cudaFuncSetAttribute(row_pass_kernel<T, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    SBD_CUDA(cudaFuncSetAttribute(row_pass_kernel<T, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    SBD_CUDA(cudaFuncSetAttribute(row_pass_kernel<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    SBD_CUDA(cudaFuncSetAttribute(ab_pass_kernel<T, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    SBD_CUDA(cudaFuncSetAttribute(ab_pass_kernel<T, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    SBD_CUDA(cudaFuncSetAttribute(ab_pass_kernel<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+}
+
+template <typename T>
+void launch_row(const RowArgs<T> &a, const PassCfg &p, int num_sms, cudaStream_t s)
+{
+    const int64_t groups = (a.nrow + p.R - 1) / p.R;
+    const int grid = (int)(groups < 65535 ? groups : 65535);
+    (void)num_sms;
+    if (!p.staged) row_pass_kernel<T, 1, false><<<grid, kThreads, p.smem, s>>>(a);
+    else if (p.R == 4) row_pass_kernel<T, (sizeof(T) == 4 ? 4 : 2), true><<<grid, kThreads, p.smem, s>>>(a);
+    else if (p.R == 2) row_pass_kernel<T, 2, true><<<grid, kThreads, p.smem, s>>>(a);
+    else row_pass_kernel<T, 1, true><<<grid, kThreads, p.smem, s>>>(a);
+    SBD_LAUNCH("row_pass_kernel");
+}
+
+template <typename T>
+void launch_ab(const AbArgs<T> &a, const PassCfg &p, cudaStream_t s)
+{
+    const int grid = (int)(a.nA < 65535 ? a.nA : 65535);
+    if (!p.staged) ab_pass_kernel<T, 1, false><<<grid, kThreads, p.smem, s>>>(a);
+    else if (p.R == 4) ab_pass_kernel<T, (sizeof(T) == 4 ? 4 : 2), true><<<grid, kThreads, p.smem, s>>>(a);
+    else if (p.R == 2) ab_pass_kernel<T, 2, true><<<grid, kThreads, p.smem, s>>>(a);
+    else ab_pass_kernel<T, 1, true><<<grid, kThreads, p.smem, s>>>(a);
+    SBD_LAUNCH("ab_pass_kernel");
+}
+
+template <typename T>
+void transpose(const T *in, T *out, int64_t rows, int64_t cols, cudaStream_t s)
+{
+    const int64_t gy = (rows + 31) / 32;
+    if (gy > 65535) fail(SBD_ERR_UNSUPPORTED, "alpha string set too large for the transpose");
+    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)gy);
+    transpose_kernel<T><<<grid, dim3(32, 8), 0, s>>>(in, out, rows, cols);
+    SBD_LAUNCH("transpose_kernel");
+}
+
+// Runs launch(); when timing is on, brackets it with events on stream s and
+// queues the pair for sbd_kernel_times (slot: kernel kind, +4 for FP32).
+template <typename F>
+void timed(Ctx &c, int slot, cudaStream_t s, F &&launch)
+{
+    if (!c.opt.timing) {
+        launch();
+        return;
+    }
+    cudaEvent_t a = take_event(c), b = take_event(c);
+    SBD_CUDA(cudaEventRecord(a, s));
+    launch();
+    SBD_CUDA(cudaEventRecord(b, s));
+    c.pending.push_back({slot, a, b});
+}
+
+template <typename T>
+void apply(Ctx &c, const T *C, double *S, const double *c64, cudaStream_t s)
+{
+    const int n2 = c.norb * c.norb;
+    const int rmax = sizeof(T) == 4 ? 4 : 2;
+    const size_t lim = smem_limit(c);
+    const SpinTables &ta = c.sp[0], &tb = c.sp[1];
+    const bool fp32 = sizeof(T) == 4;
+    const int base = fp32 ? 4 : 0;
+    T *Ct = static_cast<T *>(c.work_t);
+    timed(c, base + 0, s, [&] { transpose<T>(C, Ct, c.nA, c.nB, s); });
+
+    RowArgs<T> rb{};
+    rb.X = C;
+    rb.nrow = c.nA;
+    rb.ncol = c.nB;
+    rb.Y = S;
+    rb.y_rs = c.nB;
+    rb.y_cs = 1;
+    rb.accumulate = 0;
+    rb.hd = c.hd;
+    rb.xd64 = c64;
+    rb.row_strings = ta.strings;
+    rb.norb = c.norb;
+    rb.eri = c.eri64;
+    rb.s_ptr = tb.s_ptr;
+    rb.s_j = tb.s_j;
+    rb.s_code = tb.s_code;
+    rb.s_v = fp32 ? (const T *)tb.s_v32 : (const T *)tb.s_v64;
+    rb.d_ptr = tb.d_ptr;
+    rb.d_j = tb.d_j;
+    rb.d_v = fp32 ? (const T *)tb.d_v32 : (const T *)tb.d_v64;
+    timed(c, base + 1, s, [&] { launch_row<T>(rb, choose(c.nB, n2, sizeof(T), rmax, lim), c.num_sms, s); });
+
+    RowArgs<T> ra = rb;
+    ra.X = Ct;
+    ra.nrow = c.nB;
+    ra.ncol = c.nA;
+    ra.y_rs = 1;
+    ra.y_cs = c.nB;
+    ra.accumulate = 1;
+    ra.hd = nullptr;
+    ra.xd64 = nullptr;
+    ra.row_strings = tb.strings;
+    ra.s_ptr = ta.s_ptr;
+    ra.s_j = ta.s_j;
+    ra.s_code = ta.s_code;
+    ra.s_v = fp32 ? (const T *)ta.s_v32 : (const T *)ta.s_v64;
+    ra.d_ptr = ta.d_ptr;
+    ra.d_j = ta.d_j;
+    ra.d_v = fp32 ? (const T *)ta.d_v32 : (const T *)ta.d_v64;
+    timed(c, base + 2, s, [&] { launch_row<T>(ra, choose(c.nA, n2, sizeof(T), rmax, lim), c.num_sms, s); });
+
+    AbArgs<T> ab{};
+    ab.C = C;
+    ab.S = S;
+    ab.nA = c.nA;
+    ab.nB = c.nB;
+    ab.norb = c.norb;
+    ab.eri = fp32 ? (const T *)c.eri32 : (const T *)c.eri64;
+    ab.as_ptr = ta.s_ptr;
+    ab.as_j = ta.s_j;
+    ab.as_code = ta.s_code;
+    ab.bs_ptr = tb.s_ptr;
+    ab.bs_j = tb.s_j;
+    ab.bs_code = tb.s_code;
+    timed(c, base + 3, s, [&] { launch_ab<T>(ab, choose(c.nB, n2, sizeof(T), rmax, lim), s); });
+}
+
+}  // namespace
+
+void sigma_prepare(Ctx &c)
+{
+    set_attrs<double>(c.smem_optin);
+    set_attrs<float>(c.smem_optin);
+}
+
+void sigma_apply(Ctx &c, const void *cvec, double *svec, sbd_precision prec, cudaStream_t s, const double *c64)
+{
+    if (prec == SBD_FP64) apply<double>(c, static_cast<const double *>(cvec), svec, nullptr, s);
+    else apply<float>(c, static_cast<const float *>(cvec), svec, c64, s);
+}
+
+}  // namespace sbd

@@ -1,0 +1,495 @@
+// Excitation tables, same-spin string matrix elements and the Hamiltonian
+// diagonal.
+//
+// For one spin's sorted string set S, the singles and doubles tables list,
+// for every source string S_i, the strings S_j of the set that differ from
+// it by moving one (single) or two (double) electrons -- the per-string
+// excitation lists the sigma product iterates over (paper Sec. III-B,
+// Listing 3) -- in canonical CSR form (targets ascending).  Two builders
+// produce identical tables:
+//   all-pairs  : XOR-popcount of S_i against every S_j (popcount 2 -> single,
+//                4 -> double), a warp per source, ballots place the hits;
+//   enumerate  : every single/double move of S_i is generated and looked up
+//                with the warp-cooperative search; hits are marked in a
+//                per-warp bitmap that is then read back in ascending order.
+// Fermionic phases are popcount masks over the ket string (Jordan-Wigner
+// order within one spin):
+//   single q -> p : (-1)^popcount(S_j & bits strictly between p and q)
+//                 = <S_i| a+_p a_q |S_j>;
+//   double q1<q2 -> p1<p2 : phase(S_j, q2->p2) * phase(S_j', q1->p1), S_j' =
+//                 S_j with q2 -> p2, which equals <S_i|a+_p1 a+_p2 a_q2 a_q1|S_j>.
+// Matrix elements (Slater-Condon rules, Sec. II-B Eq. 4, for one spin):
+//   diagonal  sum_{i in S} h_ii + 1/2 sum_{i,j in S} [(ii|jj) - (ij|ji)]
+//   single    phase * [h_pq + sum_{k in S_j} ((pq|kk) - (pk|kq))]
+//   double    phase * [(p1 q1|p2 q2) - (p1 q2|p2 q1)]
+#include "common.cuh"
+
+namespace sbd {
+
+namespace {
+
+__device__ __forceinline__ double eri_at(const double *__restrict__ eri, int norb, int p, int q, int r, int s)
+{
+    return __ldg(eri + ((((size_t)p * norb + q) * norb + r) * norb + s));
+}
+
+// bits strictly between positions a and b
+__device__ __forceinline__ uint64_t between_mask(int a, int b)
+{
+    const int lo = min(a, b), hi = max(a, b);
+    const uint64_t below_hi = (1ull << hi) - 1ull;  // hi <= 63
+    const uint64_t upto_lo = (lo >= 63) ? ~0ull : ((1ull << (lo + 1)) - 1ull);
+    return below_hi & ~upto_lo;
+}
+
+__device__ __forceinline__ int move_phase(uint64_t ket, int from, int to)
+{
+    return (__popcll(ket & between_mask(from, to)) & 1) ? -1 : 1;
+}
+
+struct Entry {
+    int32_t j;
+    uint8_t orb[4];
+    int8_t sign;
+    double val;
+};
+
+__device__ Entry make_single(uint64_t si, uint64_t sj, int32_t j, int norb, const double *__restrict__ h,
+                             const double *__restrict__ eri)
+{
+    Entry e;
+    const uint64_t x = si ^ sj;
+    const int p = __ffsll((long long)(x & si)) - 1;
+    const int q = __ffsll((long long)(x & sj)) - 1;
+    const int sg = move_phase(sj, q, p);
+    double v = __ldg(h + (size_t)p * norb + q);
+    for (uint64_t m = sj; m; m &= m - 1ull) {
+        const int k = __ffsll((long long)m) - 1;
+        v += eri_at(eri, norb, p, q, k, k) - eri_at(eri, norb, p, k, k, q);
+    }
+    e.j = j;
+    e.orb[0] = (uint8_t)p;
+    e.orb[1] = 255;
+    e.orb[2] = (uint8_t)q;
+    e.orb[3] = 255;
+    e.sign = (int8_t)sg;
+    e.val = sg * v;
+    return e;
+}
+
+__device__ Entry make_double(uint64_t si, uint64_t sj, int32_t j, int norb, const double *__restrict__ eri)
+{
+    Entry e;
+    const uint64_t x = si ^ sj, pb = x & si, qb = x & sj;
+    const int p1 = __ffsll((long long)pb) - 1, p2 = 63 - __clzll((long long)pb);
+    const int q1 = __ffsll((long long)qb) - 1, q2 = 63 - __clzll((long long)qb);
+    const int s2 = move_phase(sj, q2, p2);
+    const uint64_t sj2 = sj ^ (1ull << q2) ^ (1ull << p2);
+    const int s1 = move_phase(sj2, q1, p1);
+    const int sg = s1 * s2;
+    const double v = eri_at(eri, norb, p1, q1, p2, q2) - eri_at(eri, norb, p1, q2, p2, q1);
+    e.j = j;
+    e.orb[0] = (uint8_t)p1;
+    e.orb[1] = (uint8_t)p2;
+    e.orb[2] = (uint8_t)q1;
+    e.orb[3] = (uint8_t)q2;
+    e.sign = (int8_t)sg;
+    e.val = sg * v;
+    return e;
+}
+
+struct TableOut {
+    const int64_t *s_ptr, *d_ptr;
+    int32_t *s_j, *d_j;
+    uint8_t *s_orb, *d_orb;
+    int8_t *s_sign, *d_sign;
+    int32_t *s_code;
+    double *s_v, *d_v;
+};
+
+__device__ __forceinline__ void store_single(const TableOut &o, int64_t pos, const Entry &e, int norb)
+{
+    o.s_j[pos] = e.j;
+    o.s_orb[4 * pos + 0] = e.orb[0];
+    o.s_orb[4 * pos + 1] = e.orb[1];
+    o.s_orb[4 * pos + 2] = e.orb[2];
+    o.s_orb[4 * pos + 3] = e.orb[3];
+    o.s_sign[pos] = e.sign;
+    o.s_v[pos] = e.val;
+    int32_t code = e.orb[0] * norb + e.orb[2];
+    if (e.sign < 0) code |= (int32_t)0x80000000;
+    o.s_code[pos] = code;
+}
+
+__device__ __forceinline__ void store_double(const TableOut &o, int64_t pos, const Entry &e)
+{
+    o.d_j[pos] = e.j;
+    o.d_orb[4 * pos + 0] = e.orb[0];
+    o.d_orb[4 * pos + 1] = e.orb[1];
+    o.d_orb[4 * pos + 2] = e.orb[2];
+    o.d_orb[4 * pos + 3] = e.orb[3];
+    o.d_sign[pos] = e.sign;
+    o.d_v[pos] = e.val;
+}
+
+// ---- all-pairs builder -----------------------------------------------------
+
+__global__ void pairs_count_kernel(const uint64_t *__restrict__ S, int64_t n, int64_t *cnt_s, int64_t *cnt_d)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; i < n; i += nw) {
+        const uint64_t si = S[i];
+        int64_t cs = 0, cd = 0;
+        for (int64_t j0 = 0; j0 < n; j0 += 32) {
+            const int64_t j = j0 + lane;
+            const int pc = j < n ? __popcll(si ^ __ldg(S + j)) : 0;
+            cs += __popc(__ballot_sync(0xffffffffu, pc == 2));
+            cd += __popc(__ballot_sync(0xffffffffu, pc == 4));
+        }
+        if (lane == 0) {
+            cnt_s[i] = cs;
+            cnt_d[i] = cd;
+        }
+    }
+}
+
+__global__ void pairs_fill_kernel(const uint64_t *__restrict__ S, int64_t n, int norb,
+                                  const double *__restrict__ h, const double *__restrict__ eri, TableOut o)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; i < n; i += nw) {
+        const uint64_t si = S[i];
+        int64_t ps = o.s_ptr[i], pd = o.d_ptr[i];
+        for (int64_t j0 = 0; j0 < n; j0 += 32) {
+            const int64_t j = j0 + lane;
+            const uint64_t sj = j < n ? __ldg(S + j) : si;
+            const int pc = __popcll(si ^ sj);
+            const unsigned bs = __ballot_sync(0xffffffffu, pc == 2);
+            const unsigned bd = __ballot_sync(0xffffffffu, pc == 4);
+            if (pc == 2) store_single(o, ps + __popc(bs & lt), make_single(si, sj, (int32_t)j, norb, h, eri), norb);
+            if (pc == 4) store_double(o, pd + __popc(bd & lt), make_double(si, sj, (int32_t)j, norb, eri));
+            ps += __popc(bs);
+            pd += __popc(bd);
+        }
+    }
+}
+
+// ---- enumerate + lookup builder ---------------------------------------------
+
+constexpr int kEnumWarps = 4;
+
+// pair index k in [0, m(m-1)/2) -> (x, y), x < y, in lexicographic order
+__device__ __forceinline__ void unrank_pair(int k, int m, int &x, int &y)
+{
+    x = 0;
+    while (k >= m - 1 - x) {
+        k -= m - 1 - x;
+        ++x;
+    }
+    y = x + 1 + k;
+}
+
+__device__ void mark_hits(const uint64_t *__restrict__ S, int64_t n, uint64_t t, bool valid, unsigned *bitmap)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned todo = __ballot_sync(0xffffffffu, valid);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1u;
+        const uint64_t key = __shfl_sync(0xffffffffu, t, src);
+        const int64_t idx = warp_find(S, n, key);
+        if (lane == 0 && idx >= 0) atomicOr(bitmap + (idx >> 5), 1u << (idx & 31));
+    }
+}
+
+// mode 0: counts, mode 1: fill
+__global__ void enum_kernel(const uint64_t *__restrict__ S, int64_t n, int norb, int nel, int mode,
+                            int64_t *cnt_s, int64_t *cnt_d, const double *__restrict__ h,
+                            const double *__restrict__ eri, TableOut o)
+{
+    extern __shared__ unsigned smem_u[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t words = (n + 31) / 32;
+    unsigned *bitmap = smem_u + (size_t)wib * words;
+    __shared__ uint8_t occ_s[kEnumWarps][64], vir_s[kEnumWarps][64];
+    uint8_t *occ = occ_s[wib], *vir = vir_s[wib];
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t nw = (int64_t)gridDim.x * kEnumWarps;
+    const int no = nel, nv = norb - nel;
+    for (int64_t i = blockIdx.x * (int64_t)kEnumWarps + wib; i < n; i += nw) {
+        const uint64_t si = S[i];
+        int oseen = 0, vseen = 0;
+        for (int half = 0; half < 2; ++half) {
+            const int m = lane + 32 * half;
+            const bool inr = m < norb;
+            const bool isocc = inr && ((si >> m) & 1ull);
+            const unsigned mo = __ballot_sync(0xffffffffu, isocc);
+            const unsigned mv = __ballot_sync(0xffffffffu, inr && !isocc);
+            if (isocc) occ[oseen + __popc(mo & lt)] = (uint8_t)m;
+            if (inr && !isocc) vir[vseen + __popc(mv & lt)] = (uint8_t)m;
+            oseen += __popc(mo);
+            vseen += __popc(mv);
+        }
+        for (int64_t w = lane; w < words; w += 32) bitmap[w] = 0u;
+        __syncwarp();
+        const int nsc = no * nv;
+        for (int c0 = 0; c0 < nsc; c0 += 32) {
+            const int cidx = c0 + lane;
+            const bool valid = cidx < nsc;
+            uint64_t t = 0;
+            if (valid) t = si ^ (1ull << occ[cidx / nv]) ^ (1ull << vir[cidx % nv]);
+            mark_hits(S, n, t, valid, bitmap);
+        }
+        const int npo = no * (no - 1) / 2, npv = nv * (nv - 1) / 2;
+        const int64_t ndc = (int64_t)npo * npv;
+        for (int64_t c0 = 0; c0 < ndc; c0 += 32) {
+            const int64_t cidx = c0 + lane;
+            const bool valid = cidx < ndc;
+            uint64_t t = 0;
+            if (valid) {
+                int a1, a2, b1, b2;
+                unrank_pair((int)(cidx / npv), no, a1, a2);
+                unrank_pair((int)(cidx % npv), nv, b1, b2);
+                t = si ^ (1ull << occ[a1]) ^ (1ull << occ[a2]) ^ (1ull << vir[b1]) ^ (1ull << vir[b2]);
+            }
+            mark_hits(S, n, t, valid, bitmap);
+        }
+        __syncwarp();
+        int64_t ps = mode ? o.s_ptr[i] : 0, pd = mode ? o.d_ptr[i] : 0;
+        for (int64_t w0 = 0; w0 < words; w0 += 32) {
+            const int64_t w = w0 + lane;
+            const unsigned bits = w < words ? bitmap[w] : 0u;
+            int cs = 0, cd = 0;
+            for (unsigned b = bits; b; b &= b - 1u) {
+                const int64_t j = w * 32 + (__ffs(b) - 1);
+                const int pc = __popcll(si ^ __ldg(S + j));
+                cs += pc == 2;
+                cd += pc == 4;
+            }
+            // exclusive warp prefix of (cs, cd)
+            int xs = cs, xd = cd;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int ys = __shfl_up_sync(0xffffffffu, xs, off);
+                const int yd = __shfl_up_sync(0xffffffffu, xd, off);
+                if (lane >= off) {
+                    xs += ys;
+                    xd += yd;
+                }
+            }
+            const int ts = __shfl_sync(0xffffffffu, xs, 31), td = __shfl_sync(0xffffffffu, xd, 31);
+            if (mode) {
+                int64_t qs = ps + xs - cs, qd = pd + xd - cd;
+                for (unsigned b = bits; b; b &= b - 1u) {
+                    const int64_t j = w * 32 + (__ffs(b) - 1);
+                    const uint64_t sj = __ldg(S + j);
+                    const int pc = __popcll(si ^ sj);
+                    if (pc == 2) store_single(o, qs++, make_single(si, sj, (int32_t)j, norb, h, eri), norb);
+                    else if (pc == 4) store_double(o, qd++, make_double(si, sj, (int32_t)j, norb, eri));
+                }
+            }
+            ps += ts;
+            pd += td;
+        }
+        if (!mode && lane == 0) {
+            cnt_s[i] = ps;
+            cnt_d[i] = pd;
+        }
+        __syncwarp();
+    }
+    (void)lt;
+}
+
+// ---- scan, diagonal energies, conversions, Hamiltonian diagonal ---------------
+
+// ptr[0] = 0, ptr[i+1] = ptr[i] + cnt[i]; one CTA, each thread a contiguous chunk
+__global__ void __launch_bounds__(1024) scan_kernel(const int64_t *cnt, int64_t n, int64_t *ptr)
+{
+    __shared__ int64_t part[1024];
+    const int tid = threadIdx.x;
+    const int64_t chunk = (n + 1023) / 1024;
+    const int64_t b = tid * chunk, e = min(n, b + chunk);
+    int64_t s = 0;
+    for (int64_t i = b; i < e; ++i) s += cnt[i];
+    part[tid] = s;
+    __syncthreads();
+    if (tid == 0) {
+        int64_t run = 0;
+        for (int t = 0; t < 1024; ++t) {
+            const int64_t v = part[t];
+            part[t] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    int64_t run = part[tid];
+    if (tid == 0) ptr[0] = 0;
+    for (int64_t i = b; i < e; ++i) {
+        run += cnt[i];
+        ptr[i + 1] = run;
+    }
+}
+
+__global__ void ediag_kernel(const uint64_t *S, int64_t n, int norb, const double *__restrict__ h,
+                             const double *__restrict__ eri, double *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t s = S[i];
+        double one = 0.0, two = 0.0;
+        for (uint64_t a = s; a; a &= a - 1ull) {
+            const int p = __ffsll((long long)a) - 1;
+            one += __ldg(h + (size_t)p * norb + p);
+            for (uint64_t b = s; b; b &= b - 1ull) {
+                const int q = __ffsll((long long)b) - 1;
+                two += eri_at(eri, norb, p, p, q, q) - eri_at(eri, norb, p, q, q, p);
+            }
+        }
+        out[i] = one + 0.5 * two;
+    }
+}
+
+__global__ void to_float_kernel(const double *in, float *out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __double2float_rn(in[i]);
+}
+
+// Hd[ia, ib] = E_alpha(ia) + E_beta(ib) + sum_{p in ia, r in ib} (pp|rr)   (Sec. II-E)
+__global__ void hdiag_kernel(const uint64_t *__restrict__ A, const uint64_t *__restrict__ B,
+                             const double *__restrict__ eA, const double *__restrict__ eB,
+                             const double *__restrict__ eri, int norb, int64_t nA, int64_t nB, double *hd)
+{
+    __shared__ double jd[64];
+    for (int64_t ia = blockIdx.x; ia < nA; ia += gridDim.x) {
+        const uint64_t a = A[ia];
+        if (threadIdx.x < norb) {
+            const int r = threadIdx.x;
+            double s = 0.0;
+            for (uint64_t m = a; m; m &= m - 1ull) {
+                const int p = __ffsll((long long)m) - 1;
+                s += eri_at(eri, norb, p, p, r, r);
+            }
+            jd[r] = s;
+        }
+        __syncthreads();
+        const double ea = eA[ia];
+        for (int64_t ib = threadIdx.x; ib < nB; ib += blockDim.x) {
+            double v = ea + eB[ib];
+            for (uint64_t m = B[ib]; m; m &= m - 1ull) v += jd[__ffsll((long long)m) - 1];
+            hd[ia * nB + ib] = v;
+        }
+        __syncthreads();
+    }
+}
+
+int blocks_for(int64_t n, int threads, int cap = 65535)
+{
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+}  // namespace
+
+void to_float(const double *in, float *out, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return;
+    to_float_kernel<<<blocks_for(n, 256, 16384), 256, 0, s>>>(in, out, n);
+    SBD_LAUNCH("to_float_kernel");
+}
+
+void build_tables(Ctx &c, int spin)
+{
+    SpinTables &t = c.sp[spin];
+    const int64_t n = t.n;
+    const int norb = c.norb;
+    int64_t *cnt = dalloc_n<int64_t>(c, 2 * (size_t)n);
+    t.s_ptr = dalloc_n<int64_t>(c, n + 1);
+    t.d_ptr = dalloc_n<int64_t>(c, n + 1);
+
+    int algo = c.opt.table_algo;
+    if (algo == 0) {
+        // all-pairs costs n^2/32 warp steps; enumeration about n * moves * (log32 n + 1)
+        double moves = (double)t.nel * (norb - t.nel) +
+                       0.25 * t.nel * (t.nel - 1.0) * (norb - t.nel) * (norb - t.nel - 1.0);
+        double steps = 1.0;
+        for (double r = (double)n; r > 32.0; r /= 32.0) steps += 1.0;
+        algo = ((double)n / 32.0 > moves * steps && n <= (1 << 17)) ? 2 : 1;
+    }
+    if (algo == 2 && n > (1 << 17)) fail(SBD_ERR_UNSUPPORTED, "enumerate+lookup tables need |S| <= 131072");
+    const int64_t words = (n + 31) / 32;
+    const size_t enum_smem = (size_t)kEnumWarps * words * sizeof(unsigned);
+    int warps_per_block = 8, threads = 256;
+    int grid = blocks_for(n, warps_per_block, 4 * 65535);
+    grid = grid > 65535 ? 65535 : grid;
+    TableOut o{};
+    if (algo == 1) {
+        pairs_count_kernel<<<grid, threads, 0, c.stream>>>(t.strings, n, cnt, cnt + n);
+        SBD_LAUNCH("pairs_count_kernel");
+    } else {
+        SBD_CUDA(cudaFuncSetAttribute(enum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)enum_smem));
+        int eg = blocks_for(n, kEnumWarps, 65535);
+        enum_kernel<<<eg, 32 * kEnumWarps, enum_smem, c.stream>>>(t.strings, n, norb, t.nel, 0, cnt, cnt + n,
+                                                                  c.h64, c.eri64, o);
+        SBD_LAUNCH("enum_kernel(count)");
+    }
+    scan_kernel<<<1, 1024, 0, c.stream>>>(cnt, n, t.s_ptr);
+    scan_kernel<<<1, 1024, 0, c.stream>>>(cnt + n, n, t.d_ptr);
+    SBD_LAUNCH("scan_kernel");
+    SBD_CUDA(cudaMemcpyAsync(&t.ns, t.s_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, c.stream));
+    SBD_CUDA(cudaMemcpyAsync(&t.nd, t.d_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, c.stream));
+    SBD_CUDA(cudaStreamSynchronize(c.stream));
+    if (t.ns > 0x7fffffffLL || t.nd > 0x7fffffffLL) fail(SBD_ERR_UNSUPPORTED, "excitation table too large");
+
+    t.s_j = dalloc_n<int32_t>(c, t.ns);
+    t.s_orb = dalloc_n<uint8_t>(c, 4 * t.ns);
+    t.s_sign = dalloc_n<int8_t>(c, t.ns);
+    t.s_code = dalloc_n<int32_t>(c, t.ns);
+    t.s_v64 = dalloc_n<double>(c, t.ns);
+    t.s_v32 = dalloc_n<float>(c, t.ns);
+    t.d_j = dalloc_n<int32_t>(c, t.nd);
+    t.d_orb = dalloc_n<uint8_t>(c, 4 * t.nd);
+    t.d_sign = dalloc_n<int8_t>(c, t.nd);
+    t.d_v64 = dalloc_n<double>(c, t.nd);
+    t.d_v32 = dalloc_n<float>(c, t.nd);
+    o.s_ptr = t.s_ptr;
+    o.d_ptr = t.d_ptr;
+    o.s_j = t.s_j;
+    o.d_j = t.d_j;
+    o.s_orb = t.s_orb;
+    o.d_orb = t.d_orb;
+    o.s_sign = t.s_sign;
+    o.d_sign = t.d_sign;
+    o.s_code = t.s_code;
+    o.s_v = t.s_v64;
+    o.d_v = t.d_v64;
+    if (algo == 1) {
+        pairs_fill_kernel<<<grid, threads, 0, c.stream>>>(t.strings, n, norb, c.h64, c.eri64, o);
+        SBD_LAUNCH("pairs_fill_kernel");
+    } else {
+        int eg = blocks_for(n, kEnumWarps, 65535);
+        enum_kernel<<<eg, 32 * kEnumWarps, enum_smem, c.stream>>>(t.strings, n, norb, t.nel, 1, nullptr, nullptr,
+                                                                  c.h64, c.eri64, o);
+        SBD_LAUNCH("enum_kernel(fill)");
+    }
+    to_float(t.s_v64, t.s_v32, t.ns, c.stream);
+    to_float(t.d_v64, t.d_v32, t.nd, c.stream);
+    t.ediag = dalloc_n<double>(c, n);
+    ediag_kernel<<<blocks_for(n, 128), 128, 0, c.stream>>>(t.strings, n, norb, c.h64, c.eri64, t.ediag);
+    SBD_LAUNCH("ediag_kernel");
+    dfree(c, cnt);
+}
+
+void build_diagonal(Ctx &c)
+{
+    c.hd = dalloc_n<double>(c, (size_t)c.N);
+    int grid = (int)(c.nA < 65535 ? c.nA : 65535);
+    hdiag_kernel<<<grid, 256, 0, c.stream>>>(c.sp[0].strings, c.sp[1].strings, c.sp[0].ediag, c.sp[1].ediag,
+                                             c.eri64, c.norb, c.nA, c.nB, c.hd);
+    SBD_LAUNCH("hdiag_kernel");
+}
+
+}  // namespace sbd

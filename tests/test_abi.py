@@ -1,0 +1,63 @@
+"""The C-ABI library loads and exports every entry point its header declares (no GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2601_16637_gb300 import binding as b
+from paper_2601_16637_gb300 import build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "sbd.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(sbd_[a-z_0-9]+)\s*\(", text))
+    return sorted(n for n in names if not n.endswith("_fn"))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return b.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(b._SIGNATURES) == set(names)
+
+
+def test_struct_layouts_match_header():
+    # sbd_options: double, int, int, size_t, double, int, int, fn, fn, void*, int (+4 padding)  (LP64)
+    assert ctypes.sizeof(b.sbd_options) == 8 + 4 + 4 + 8 + 8 + 4 + 4 + 8 + 8 + 8 + 4 + 4
+    assert ctypes.sizeof(b.sbd_report) == 6 * 4 + 3 * 8
+
+
+def test_defaults_and_status_strings(lib):
+    o = b.sbd_default_options()
+    assert o.delta == 1e-4 and o.max_iter == 200 and o.max_subspace == 0 and not o.alloc
+    assert b.sbd_status_string(0) == "ok"
+    assert b.sbd_status_string(-3) == "duplicate string"
+
+
+def test_host_side_argument_errors_need_no_gpu(lib):
+    z = np.zeros(1)
+    s = np.ones(1, dtype=np.uint64)
+    with pytest.raises(b.SbdError) as e:
+        b.sbd_create(65, 1, 1, z, z, s, s, stream=0)
+    assert e.value.code == -4
+    with pytest.raises(b.SbdError) as e:
+        b.sbd_create(4, 5, 1, z, z, s, s, stream=0)
+    assert e.value.code == -1
+    out = ctypes.c_void_p()
+    assert lib.sbd_create(None, 4, 1, 1, None, None, None, 1, None, 1, None, None) == -1
+    assert lib.sbd_create(ctypes.byref(out), 4, 1, 1, None, None, None, 1, None, 1, None, None) == -1
+    assert lib.sbd_destroy(None) == -1
+    assert lib.sbd_sigma(None, None, None, 1, 0, None) == -1
+    assert lib.sbd_davidson(None, 1, 1e-8, 0, None, None, None, None) == -1

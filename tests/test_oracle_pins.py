@@ -198,6 +198,15 @@ def test_sigma_equals_dense_product_and_is_hermitian(oracle_mod):
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
 
 
+def test_explicit_csr_equals_dense(oracle_mod):
+    # the assembled matrix (Sec. II-A, explicit) holds exactly the dense H's nonzeros
+    wl = W.make("t", 10, 3, 3, 45, 40, 0.3, seed=4)
+    o = oracle_mod.Oracle.from_workload(wl)
+    H = o.dense()
+    Hs = o.csr().toarray()
+    assert np.array_equal(Hs, H)
+
+
 def test_sigma_rows_match_full_sigma(oracle_mod):
     wl = W.make("t", 12, 4, 4, 150, 140, 0.3, seed=3)
     o = oracle_mod.Oracle.from_workload(wl)
