@@ -376,7 +376,6 @@ def main():
         A_h = torch.from_numpy(wl.A.view(np.int64)).pin_memory()
         B_h = torch.from_numpy(wl.B.view(np.int64)).pin_memory()
         vec_h = torch.empty((wl.nroots, wl.ndets), dtype=torch.float64, pin_memory=True)
-        step(h_h, eri_h, A_h, B_h, vec_h)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()

@@ -25,6 +25,15 @@ void count_launch();
 #define SBD_CUDA(call) ::sbd::check_cuda((call), #call, __FILE__, __LINE__)
 #define SBD_LAUNCH(what) (::sbd::count_launch(), ::sbd::check_cuda(cudaGetLastError(), what, __FILE__, __LINE__))
 
+// packed single-excitation entries: strings per spin must stay below 2^18
+constexpr int kPackJBits = 18;
+constexpr uint32_t kPackJMask = (1u << kPackJBits) - 1u;
+constexpr int kPackCodeShift = 18;
+constexpr uint32_t kPackCodeMask = 0xfffu;
+constexpr uint32_t kPackNegBit = 1u << 30;
+constexpr int64_t kMaxStringsPerSpin = (int64_t)1 << kPackJBits;
+constexpr int kBankGroups = 8;  // 16-byte bank groups of shared memory (32 banks x 4 bytes)
+
 // ---------------------------------------------------------------------------
 // device status words written by validation kernels
 
@@ -48,9 +57,18 @@ struct SpinTables {
     int32_t *s_j = nullptr, *d_j = nullptr;      // target index
     uint8_t *s_orb = nullptr, *d_orb = nullptr;  // p1,p2,q1,q2 per entry
     int8_t *s_sign = nullptr, *d_sign = nullptr; // fermionic phase
-    int32_t *s_code = nullptr;  // p*norb+q of a single, bit 31 set when the phase is -1
+    // packed single: target j (bits 0-17) | code p*norb+q (bits 18-29) | phase -1 (bit 30)
+    uint32_t *s_pk = nullptr;
     double *s_v64 = nullptr, *d_v64 = nullptr;   // same-spin matrix elements
-    float *s_v32 = nullptr, *d_v32 = nullptr;
+    // Sigma copies of the lists: the same entries per source, reordered so that every aligned
+    // block of 8 entries has distinct targets modulo 8 where possible (kBankGroups); a block of 8
+    // lanes then gathers 16-byte staged rows from distinct shared-memory bank groups.
+    uint32_t *s_pk_sig = nullptr;
+    double *s_v64_sig = nullptr;
+    int32_t *d_j_sig = nullptr;
+    double *d_v64_sig = nullptr;
+    uint2 *s_pkv32 = nullptr;  // (s_pk_sig, FP32 value bits), for the mixed sigma
+    uint2 *d_jv32 = nullptr;   // (d_j_sig, FP32 value bits), for the mixed sigma
     double *ediag = nullptr;     // [n] same-spin diagonal energies
     int max_singles = 0;         // longest singles list
     bool alias = false;          // storage owned by the other spin (A == B)

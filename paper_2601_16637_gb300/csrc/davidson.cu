@@ -1,21 +1,27 @@
 // Block Davidson on the device (paper Sec. II-C, with the damped diagonal
 // preconditioner of Sec. II-E and the stopping tests of Sec. II-G).
 //
-// Per iteration: Rayleigh-Ritz on the projected matrix T = V^T W (cyclic
-// Jacobi in one CTA), Ritz vectors U = V Y and HU = W Y with residual norms,
-// the preconditioned corrections t = r / (sign(d) max(|d|, delta)),
-// d = Hd - theta, block classical Gram-Schmidt with one re-orthogonalisation
-// pass against the basis, and the sigma product of the new basis vectors.
-// A thick restart keeps the lowest Ritz vectors when the basis is full.
+// Per iteration: Rayleigh-Ritz on the projected matrix T = V^T W (parallel
+// Jacobi in one CTA), one fused pass for the Ritz vectors U = V Y, HU = W Y,
+// the residual norms and the preconditioned corrections
+// t = r / (sign(d) max(|d|, delta)), d = Hd - theta (Eq. 7); block classical
+// Gram-Schmidt with one re-orthogonalisation pass against the basis; and the
+// sigma product of the new basis vectors.  A thick restart keeps the lowest
+// Ritz vectors when the basis is full.
 //
 // All vectors, T, the Ritz quantities and every reduction are FP64 (two-stage
 // reductions in a fixed order, so results are reproducible).  In mixed mode
-// the sigma of new basis vectors uses FP32 amplitudes (SBD_MIXED); when the
-// residual computed from that sigma stops improving, the Ritz vectors are
-// multiplied by the FP64 sigma (defect correction): their FP64 Rayleigh
-// quotients and residuals decide convergence, and the basis restarts from
-// them with exact W columns.  Only converged FP64-evaluated residuals end
-// the solve.
+// the sigma of new basis vectors uses FP32 amplitudes (SBD_MIXED, with the
+// diagonal term taken from the FP64 vector); when the residual computed from
+// that sigma stops improving, the Ritz vectors are multiplied by the FP64
+// sigma (defect correction): their FP64 Rayleigh quotients and residuals
+// decide convergence, the basis keeps the lowest Ritz vectors with exact W
+// columns for the targets, and projected-matrix entries that pair an exact
+// column with a mixed one use the exact column, so FP32 noise does not couple
+// into the converged direction.
+//
+// The vector kernels are HBM-streaming: every thread keeps kLoad independent
+// loads in flight before it consumes them.
 #include <math.h>
 #include <stdio.h>
 
@@ -28,9 +34,12 @@ namespace sbd {
 
 namespace {
 
-constexpr int kBlas = 256;      // threads per BLAS block
-constexpr int kDotBatch = 16;   // vectors per multi-dot launch
-constexpr int kMaxSub = 64;     // largest subspace the Jacobi kernel takes
+constexpr int kBlas = 256;    // threads per BLAS block
+constexpr int kLoad = 8;      // loads each thread issues before using them
+constexpr int kDotMax = 32;   // dot products per multi-dot launch
+constexpr int kRitzMax = 16;  // vectors combined per launch
+constexpr int kMaxSub = 64;   // largest subspace the Jacobi kernel takes
+constexpr int kPart = kDotMax + 1;  // partial-sum slots per block (dots + one norm)
 
 int blas_grid(const Ctx &c, int64_t N)
 {
@@ -53,99 +62,181 @@ __device__ __forceinline__ T block_sum(T v, T *red)
     return s;  // valid in thread 0
 }
 
-// partial[b*kDotBatch + a] = sum over block b's elements of X[a][i] * y[i], a < k <= kDotBatch
+// partial[b*kPart + a] = sum over block b's elements of X[a][i] y[i] (a < k <= kDotMax);
+// with NORM also partial[b*kPart + kDotMax] = sum y[i]^2
+template <bool NORM, int KB>
 __global__ void __launch_bounds__(kBlas) mdot_partial(const double *__restrict__ X, int64_t ldx, int k,
                                                       const double *__restrict__ y, int64_t N, double *partial)
 {
     __shared__ double red[kBlas / 32];
-    double acc[kDotBatch];
+    double acc[KB];
 #pragma unroll
-    for (int a = 0; a < kDotBatch; ++a) acc[a] = 0.0;
+    for (int a = 0; a < KB; ++a) acc[a] = 0.0;
+    double an = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)kBlas + threadIdx.x; i < N; i += (int64_t)gridDim.x * kBlas) {
         const double yi = y[i];
+        if (NORM) an += yi * yi;
 #pragma unroll
-        for (int a = 0; a < kDotBatch; ++a)
-            if (a < k) acc[a] += X[a * ldx + i] * yi;
+        for (int a0 = 0; a0 < KB; a0 += kLoad) {
+            if (a0 < k) {
+                double x[kLoad];
+#pragma unroll
+                for (int u = 0; u < kLoad; ++u) x[u] = (a0 + u < k) ? X[(a0 + u) * ldx + i] : 0.0;
+#pragma unroll
+                for (int u = 0; u < kLoad; ++u) acc[a0 + u] += x[u] * yi;
+            }
+        }
     }
-    for (int a = 0; a < k; ++a) {
-        const double s = block_sum(acc[a], red);
-        if (threadIdx.x == 0) partial[blockIdx.x * kDotBatch + a] = s;
+#pragma unroll
+    for (int a = 0; a < KB; ++a)
+        if (a < k) {  // k is uniform over the block
+            const double s = block_sum(acc[a], red);
+            if (threadIdx.x == 0) partial[blockIdx.x * kPart + a] = s;
+        }
+    if (NORM) {
+        const double s = block_sum(an, red);
+        if (threadIdx.x == 0) partial[blockIdx.x * kPart + kDotMax] = s;
     }
 }
 
-// out1[a*st1] (and out2[a*st2] when given) = sum_b partial[b][a], fixed order
+// out1[a*st1] (and out2[a*st2] when given) = sum_b partial[b][a] for a < k;
+// slot kDotMax (the norm) goes to *norm2 when given.  Fixed summation order.
 __global__ void mdot_final(const double *partial, int nblocks, int k, double *out1, int64_t st1, double *out2,
-                           int64_t st2)
+                           int64_t st2, double *norm2)
 {
     const int a = threadIdx.x;
-    if (a >= k) return;
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partial[b * kDotBatch + a];
-    out1[a * st1] = s;
-    if (out2) out2[a * st2] = s;
+    if (a < k) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += partial[b * kPart + a];
+        out1[a * st1] = s;
+        if (out2) out2[a * st2] = s;
+    } else if (a == kDotMax && norm2) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += partial[b * kPart + kDotMax];
+        *norm2 = s;
+    }
 }
 
-// y -= sum_a coef[a] X[a], a < k <= kDotBatch
+// y -= sum_a coef[a] X[a] (a < k <= kMaxSub); with NORM, partial[b*kPart + kDotMax] = sum of the new y^2
+template <bool NORM>
 __global__ void __launch_bounds__(kBlas) maxpy_kernel(const double *__restrict__ X, int64_t ldx, int k,
-                                                      const double *__restrict__ coef, double *y, int64_t N)
+                                                      const double *__restrict__ coef, double *y, int64_t N,
+                                                      double *partial)
 {
-    double c[kDotBatch];
-#pragma unroll
-    for (int a = 0; a < kDotBatch; ++a) c[a] = a < k ? coef[a] : 0.0;
+    __shared__ double cs[kMaxSub];
+    __shared__ double red[kBlas / 32];
+    for (int a = threadIdx.x; a < kMaxSub; a += kBlas) cs[a] = a < k ? coef[a] : 0.0;
+    __syncthreads();
+    double an = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)kBlas + threadIdx.x; i < N; i += (int64_t)gridDim.x * kBlas) {
         double s = 0.0;
+        for (int a0 = 0; a0 < k; a0 += kLoad) {
+            double x[kLoad];
 #pragma unroll
-        for (int a = 0; a < kDotBatch; ++a)
-            if (a < k) s += c[a] * X[a * ldx + i];
-        y[i] -= s;
+            for (int u = 0; u < kLoad; ++u) x[u] = (a0 + u < k) ? X[(a0 + u) * ldx + i] : 0.0;
+#pragma unroll
+            for (int u = 0; u < kLoad; ++u) s += cs[min(a0 + u, kMaxSub - 1)] * x[u];
+        }
+        const double yn = y[i] - s;
+        y[i] = yn;
+        if (NORM) an += yn * yn;
+    }
+    if (NORM) {
+        const double s = block_sum(an, red);
+        if (threadIdx.x == 0) partial[blockIdx.x * kPart + kDotMax] = s;
     }
 }
 
-// out[j] = sum_a Y[a*ldy + j] X[a] for j < m <= kDotBatch, a < k
-__global__ void __launch_bounds__(kBlas) combine_kernel(const double *__restrict__ X, int64_t ldx, int k,
-                                                        const double *__restrict__ Y, int ldy, int m, double *out,
-                                                        int64_t ldo, int64_t N)
+// out[j] = sum_a Y[a*ldy + j] X[a] and hout[j] = sum_a Y[a*ldy + j] H[a] for j < m <= kRitzMax, a < k.
+// With RITZ (the Ritz step), also: r = hout - theta[j] out, partial[b*kPart + j] = sum r^2 and the
+// preconditioned correction tc[j] = r / (sign(d) max(|d|, delta)), d = hd - theta[j].
+template <bool RITZ, int M>
+__global__ void __launch_bounds__(kBlas) combine_kernel(const double *__restrict__ X, const double *__restrict__ H,
+                                                        int64_t ldx, int k, const double *__restrict__ Y, int ldy,
+                                                        int m, double *out, double *hout, int64_t ldo,
+                                                        const double *__restrict__ theta,
+                                                        const double *__restrict__ hd, double delta, double *tc,
+                                                        double *partial, int64_t N)
 {
-    __shared__ double ys[kMaxSub * kDotBatch];
+    __shared__ double ys[kMaxSub * kRitzMax];
+    __shared__ double th[kRitzMax];
+    __shared__ double red[kBlas / 32];
     for (int t = threadIdx.x; t < k * m; t += kBlas) ys[t] = Y[(t / m) * ldy + (t % m)];
+    if (RITZ)
+        for (int j = threadIdx.x; j < m; j += kBlas) th[j] = theta[j];
     __syncthreads();
+    double racc[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) racc[j] = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)kBlas + threadIdx.x; i < N; i += (int64_t)gridDim.x * kBlas) {
-        double acc[kDotBatch];
+        double u[M], hu[M];
 #pragma unroll
-        for (int j = 0; j < kDotBatch; ++j) acc[j] = 0.0;
-        for (int a = 0; a < k; ++a) {
-            const double x = X[a * ldx + i];
+        for (int j = 0; j < M; ++j) u[j] = hu[j] = 0.0;
+        for (int a0 = 0; a0 < k; a0 += kLoad / 2) {
+            double x[kLoad / 2], h[kLoad / 2];
 #pragma unroll
-            for (int j = 0; j < kDotBatch; ++j)
-                if (j < m) acc[j] += ys[a * m + j] * x;
+            for (int q = 0; q < kLoad / 2; ++q) {
+                const bool ok = a0 + q < k;
+                x[q] = ok ? X[(a0 + q) * ldx + i] : 0.0;
+                h[q] = ok ? H[(a0 + q) * ldx + i] : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < kLoad / 2; ++q) {
+                const int a = min(a0 + q, kMaxSub - 1);
+#pragma unroll
+                for (int j = 0; j < M; ++j)
+                    if (j < m) {
+                        u[j] += ys[a * m + j] * x[q];
+                        hu[j] += ys[a * m + j] * h[q];
+                    }
+            }
         }
 #pragma unroll
-        for (int j = 0; j < kDotBatch; ++j)
-            if (j < m) out[j * ldo + i] = acc[j];
+        for (int j = 0; j < M; ++j)
+            if (j < m) {
+                out[j * ldo + i] = u[j];
+                hout[j * ldo + i] = hu[j];
+                if (RITZ) {
+                    const double r = hu[j] - th[j] * u[j];
+                    racc[j] += r * r;
+                    const double d = hd[i] - th[j];
+                    tc[j * ldo + i] = r / ((d >= 0.0 ? 1.0 : -1.0) * fmax(fabs(d), delta));
+                }
+            }
+    }
+    if (RITZ) {
+#pragma unroll
+        for (int j = 0; j < M; ++j)
+            if (j < m) {
+                const double s = block_sum(racc[j], red);
+                if (threadIdx.x == 0) partial[blockIdx.x * kPart + j] = s;
+            }
     }
 }
 
-// partial[b*kDotBatch + j] = sum over block b of (HU[j] - theta[j] U[j])^2
+// partial[b*kPart + j] = sum over block b of (HU[j] - theta[j] U[j])^2, j < m <= kRitzMax
 __global__ void __launch_bounds__(kBlas) resid_partial(const double *__restrict__ U, const double *__restrict__ HU,
                                                        int64_t ld, int m, const double *__restrict__ theta,
                                                        int64_t N, double *partial)
 {
     __shared__ double red[kBlas / 32];
-    double acc[kDotBatch];
+    double acc[kRitzMax];
 #pragma unroll
-    for (int j = 0; j < kDotBatch; ++j) acc[j] = 0.0;
+    for (int j = 0; j < kRitzMax; ++j) acc[j] = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)kBlas + threadIdx.x; i < N; i += (int64_t)gridDim.x * kBlas) {
 #pragma unroll
-        for (int j = 0; j < kDotBatch; ++j)
+        for (int j = 0; j < kRitzMax; ++j)
             if (j < m) {
                 const double r = HU[j * ld + i] - theta[j] * U[j * ld + i];
                 acc[j] += r * r;
             }
     }
-    for (int j = 0; j < m; ++j) {
-        const double s = block_sum(acc[j], red);
-        if (threadIdx.x == 0) partial[blockIdx.x * kDotBatch + j] = s;
-    }
+#pragma unroll
+    for (int j = 0; j < kRitzMax; ++j)
+        if (j < m) {
+            const double s = block_sum(acc[j], red);
+            if (threadIdx.x == 0) partial[blockIdx.x * kPart + j] = s;
+        }
 }
 
 // t = (hu - theta u) / (sign(d) max(|d|, delta)), d = Hd - theta   (Eq. 7)
@@ -161,10 +252,11 @@ __global__ void precond_kernel(const double *__restrict__ u, const double *__res
     }
 }
 
-__global__ void scale_kernel(double *x, double s, int64_t N)
+// dst = src * s (dst may equal src)
+__global__ void scale_kernel(const double *src, double *dst, double s, int64_t N)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] *= s;
+        dst[i] = src[i] * s;
 }
 
 __global__ void set_kernel(double *x, int64_t idx, double v) { x[idx] = v; }
@@ -242,76 +334,101 @@ __global__ void argmaxabs_partial(const double *__restrict__ x, int64_t N, doubl
 }
 
 // Eigenpairs of the symmetric k x k matrix T (upper and lower parts averaged)
-// by cyclic Jacobi rotations in one CTA.  evals ascending; Y[a*ldy + j] is
-// component a of eigenvector j.
+// by parallel-order Jacobi rotations in one CTA.  Each sweep runs k-1 rounds
+// of the round-robin (tournament) pairing of the k indices; the k/2 pairs of
+// a round are disjoint, so their rotations commute and are applied together:
+// first to the columns of A and of the eigenvector matrix V, then to the rows
+// of A.  A rotation is skipped when |a_pq| is negligible against both
+// diagonal entries; the sweeps stop when a sweep rotates nothing.
+// evals ascending; Y[a*ldy + j] is component a of eigenvector j.
 __global__ void jacobi_kernel(const double *__restrict__ T, int ldt, int k, double *evals, double *Y, int ldy)
 {
     extern __shared__ double js[];
     double *A = js, *V = js + k * k;
-    __shared__ double rot[2];
-    __shared__ int flag;
-    __shared__ double red[32];
+    __shared__ int pos[kMaxSub + 1];
+    __shared__ int pp[kMaxSub / 2 + 1], qq[kMaxSub / 2 + 1];
+    __shared__ double cc[kMaxSub / 2 + 1], ss[kMaxSub / 2 + 1];
+    __shared__ int rotated;
     __shared__ int ord[kMaxSub];
-    const int tid = threadIdx.x;
-    for (int t = tid; t < k * k; t += blockDim.x) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int t = tid; t < k * k; t += nt) {
         const int i = t / k, j = t % k;
         A[t] = 0.5 * (T[i * ldt + j] + T[j * ldt + i]);
         V[t] = i == j ? 1.0 : 0.0;
     }
+    const int m = (k + 1) & ~1;  // even number of players (index k is a bye when k is odd)
+    const int half = m / 2;
+    for (int i = tid; i < m; i += nt) pos[i] = i;
     __syncthreads();
-    double fro = 0.0;
-    for (int t = tid; t < k * k; t += blockDim.x) fro += A[t] * A[t];
-    fro = block_sum(fro, red);
-    __shared__ double fro_s;
-    if (tid == 0) fro_s = sqrt(fro) > 0.0 ? sqrt(fro) : 1.0;
-    __syncthreads();
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0;
-        for (int t = tid; t < k * k; t += blockDim.x) {
-            const int i = t / k, j = t % k;
-            if (i < j) off += A[t] * A[t];
-        }
-        off = block_sum(off, red);
-        if (tid == 0) flag = sqrt(off) <= 1e-17 * fro_s;
-        __syncthreads();
-        if (flag) break;
-        for (int p = 0; p < k - 1; ++p)
-            for (int q = p + 1; q < k; ++q) {
-                if (tid == 0) {
-                    const double apq = A[p * k + q];
-                    flag = apq == 0.0;
-                    if (!flag) {
-                        const double theta = (A[q * k + q] - A[p * k + p]) / (2.0 * apq);
+    for (int sweep = 0; sweep < 60 && k > 1; ++sweep) {
+        if (tid == 0) rotated = 0;
+        for (int round = 0; round < m - 1; ++round) {
+            if (tid < half) {
+                int p = pos[tid], q = pos[m - 1 - tid];
+                if (p > q) {
+                    const int t = p;
+                    p = q;
+                    q = t;
+                }
+                double c = 1.0, s = 0.0;
+                if (q < k) {
+                    const double apq = A[p * k + q], app = A[p * k + p], aqq = A[q * k + q];
+                    const double g = 100.0 * fabs(apq);
+                    if (apq != 0.0 && !(fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq))) {
+                        const double theta = (aqq - app) / (2.0 * apq);
                         const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                        const double c = 1.0 / sqrt(t * t + 1.0);
-                        rot[0] = c;
-                        rot[1] = t * c;
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        s = t * c;
+                        rotated = 1;
+                    } else if (apq != 0.0) {
+                        A[p * k + q] = 0.0;  // negligible: set to zero, as the sequential method does
+                        A[q * k + p] = 0.0;
                     }
                 }
-                __syncthreads();
-                if (flag) {
-                    __syncthreads();
-                    continue;
-                }
-                const double c = rot[0], s = rot[1];
-                if (tid < k) {
-                    const int r = tid;
+                pp[tid] = p;
+                qq[tid] = q;
+                cc[tid] = c;
+                ss[tid] = s;
+            }
+            __syncthreads();
+            // columns p, q of A and V
+            for (int w = tid; w < half * k; w += nt) {
+                const int t = w / k, r = w % k;
+                const int p = pp[t], q = qq[t];
+                if (q < k && ss[t] != 0.0) {
+                    const double c = cc[t], s = ss[t];
                     const double arp = A[r * k + p], arq = A[r * k + q];
                     A[r * k + p] = c * arp - s * arq;
                     A[r * k + q] = s * arp + c * arq;
-                }
-                __syncthreads();
-                if (tid < k) {
-                    const int r = tid;
-                    const double apr = A[p * k + r], aqr = A[q * k + r];
-                    A[p * k + r] = c * apr - s * aqr;
-                    A[q * k + r] = s * apr + c * aqr;
                     const double vrp = V[r * k + p], vrq = V[r * k + q];
                     V[r * k + p] = c * vrp - s * vrq;
                     V[r * k + q] = s * vrp + c * vrq;
                 }
-                __syncthreads();
             }
+            __syncthreads();
+            // rows p, q of A
+            for (int w = tid; w < half * k; w += nt) {
+                const int t = w / k, r = w % k;
+                const int p = pp[t], q = qq[t];
+                if (q < k && ss[t] != 0.0) {
+                    const double c = cc[t], s = ss[t];
+                    const double apr = A[p * k + r], aqr = A[q * k + r];
+                    A[p * k + r] = c * apr - s * aqr;
+                    A[q * k + r] = s * apr + c * aqr;
+                }
+            }
+            __syncthreads();
+            // next pairing: position 0 stays, the others rotate by one
+            if (tid == 0) {
+                const int last = pos[m - 1];
+                for (int i = m - 1; i > 1; --i) pos[i] = pos[i - 1];
+                pos[1] = last;
+            }
+            __syncthreads();
+        }
+        const int any = rotated;
+        __syncthreads();
+        if (!any) break;
     }
     if (tid == 0) {
         for (int i = 0; i < k; ++i) ord[i] = i;
@@ -324,11 +441,11 @@ __global__ void jacobi_kernel(const double *__restrict__ T, int ldt, int k, doub
                 }
     }
     __syncthreads();
-    for (int t = tid; t < k * k; t += blockDim.x) {
+    for (int t = tid; t < k * k; t += nt) {
         const int a = t / k, j = t % k;
         Y[a * ldy + j] = V[a * k + ord[j]];
     }
-    for (int j = tid; j < k; j += blockDim.x) evals[j] = A[ord[j] * k + ord[j]];
+    for (int j = tid; j < k; j += nt) evals[j] = A[ord[j] * k + ord[j]];
 }
 
 // ---------------------------------------------------------------------------
@@ -339,72 +456,109 @@ struct Work {
     cudaStream_t s;
     int64_t N;
     int grid;
-    double *partial = nullptr;  // [grid][kDotBatch]
+    double *partial = nullptr;  // [grid][kPart]
+    double *dscal = nullptr;    // device scalars
     double *pv = nullptr;
     int64_t *pi = nullptr;
     std::vector<double> hpart;
     explicit Work(Ctx &cc) : c(cc), s(cc.stream), N(cc.N), grid(blas_grid(cc, cc.N)) {}
 
-    // out[a] (device, stride st) = X[a] . y, a < k
+    // out1[a*st1] (and out2[a*st2]) = X[a] . y for a < k; with norm2, also y . y
     void dots(const double *X, int64_t ldx, int k, const double *y, double *out1, int64_t st1,
-              double *out2 = nullptr, int64_t st2 = 0)
+              double *out2 = nullptr, int64_t st2 = 0, double *norm2 = nullptr)
     {
-        for (int a0 = 0; a0 < k; a0 += kDotBatch) {
-            const int kb = std::min(kDotBatch, k - a0);
-            mdot_partial<<<grid, kBlas, 0, s>>>(X + a0 * ldx, ldx, kb, y, N, partial);
+        for (int a0 = 0; a0 < k || (a0 == 0 && norm2); a0 += kDotMax) {
+            const int kb = std::min(kDotMax, k - a0);
+            const bool nrm = norm2 && a0 == 0;
+            const double *Xa = X + a0 * ldx;
+            if (kb <= 8) {
+                if (nrm) mdot_partial<true, 8><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+                else mdot_partial<false, 8><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+            } else if (kb <= 16) {
+                if (nrm) mdot_partial<true, 16><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+                else mdot_partial<false, 16><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+            } else {
+                if (nrm) mdot_partial<true, kDotMax><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+                else mdot_partial<false, kDotMax><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+            }
             SBD_LAUNCH("mdot_partial");
-            mdot_final<<<1, kDotBatch, 0, s>>>(partial, grid, kb, out1 + a0 * st1, st1,
-                                               out2 ? out2 + a0 * st2 : nullptr, st2);
+            mdot_final<<<1, kDotMax + 1, 0, s>>>(partial, grid, kb, out1 + a0 * st1, st1,
+                                                 out2 ? out2 + a0 * st2 : nullptr, st2, nrm ? norm2 : nullptr);
             SBD_LAUNCH("mdot_final");
+            if (k <= a0 + kDotMax) break;
         }
     }
-    void axpys(const double *X, int64_t ldx, int k, const double *coef, double *y)
+    // y -= X coef; with norm2, also the new y . y
+    void axpys(const double *X, int64_t ldx, int k, const double *coef, double *y, double *norm2 = nullptr)
     {
-        for (int a0 = 0; a0 < k; a0 += kDotBatch) {
-            const int kb = std::min(kDotBatch, k - a0);
-            maxpy_kernel<<<grid, kBlas, 0, s>>>(X + a0 * ldx, ldx, kb, coef + a0, y, N);
+        if (norm2) {
+            maxpy_kernel<true><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
+            SBD_LAUNCH("maxpy_kernel");
+            mdot_final<<<1, kDotMax + 1, 0, s>>>(partial, grid, 0, nullptr, 0, nullptr, 0, norm2);
+            SBD_LAUNCH("mdot_final");
+        } else {
+            maxpy_kernel<false><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
             SBD_LAUNCH("maxpy_kernel");
         }
     }
-    // out[j] = sum_a Y[a][j] X[a], j < m, a < k
-    void combine(const double *X, int64_t ldx, int k, const double *Y, int ldy, int m, double *out, int64_t ldo)
+    template <bool RITZ>
+    void launch_combine(const double *X, const double *H, int64_t ldx, int k, const double *Y, int ldy, int m,
+                        double *out, double *hout, int64_t ldo, const double *theta, const double *hd, double delta,
+                        double *tc)
     {
-        for (int j0 = 0; j0 < m; j0 += kDotBatch) {
-            const int mb = std::min(kDotBatch, m - j0);
-            combine_kernel<<<grid, kBlas, 0, s>>>(X, ldx, k, Y + j0, ldy, mb, out + j0 * ldo, ldo, N);
-            SBD_LAUNCH("combine_kernel");
+        if (m <= 1)
+            combine_kernel<RITZ, 1><<<grid, kBlas, 0, s>>>(X, H, ldx, k, Y, ldy, m, out, hout, ldo, theta, hd, delta,
+                                                           tc, partial, N);
+        else if (m <= 4)
+            combine_kernel<RITZ, 4><<<grid, kBlas, 0, s>>>(X, H, ldx, k, Y, ldy, m, out, hout, ldo, theta, hd, delta,
+                                                           tc, partial, N);
+        else if (m <= 8)
+            combine_kernel<RITZ, 8><<<grid, kBlas, 0, s>>>(X, H, ldx, k, Y, ldy, m, out, hout, ldo, theta, hd, delta,
+                                                           tc, partial, N);
+        else
+            combine_kernel<RITZ, kRitzMax><<<grid, kBlas, 0, s>>>(X, H, ldx, k, Y, ldy, m, out, hout, ldo, theta, hd,
+                                                                  delta, tc, partial, N);
+        SBD_LAUNCH("combine_kernel");
+    }
+    // out[j] = sum_a Y[a][j] X[a], hout[j] = sum_a Y[a][j] H[a], j < m, a < k
+    void combine(const double *X, const double *H, int64_t ldx, int k, const double *Y, int ldy, int m, double *out,
+                 double *hout, int64_t ldo)
+    {
+        for (int j0 = 0; j0 < m; j0 += kRitzMax) {
+            const int mb = std::min(kRitzMax, m - j0);
+            launch_combine<false>(X, H, ldx, k, Y + j0, ldy, mb, out + j0 * ldo, hout + j0 * ldo, ldo, nullptr,
+                                  nullptr, 0.0, nullptr);
         }
     }
-    double norm(const double *x, double *dscratch)
+    // the Ritz step: U, HU, the corrections tc and the residual norms (host) for j < m <= kRitzMax
+    void ritz(const double *V, const double *W, int64_t ld, int k, const double *Y, int ldy, int m, double *U,
+              double *HU, const double *theta, const double *hd, double delta, double *tc, double *rn_host)
     {
-        dots(x, 0, 1, x, dscratch, 1);
-        double v = 0.0;
-        SBD_CUDA(cudaMemcpyAsync(&v, dscratch, sizeof(double), cudaMemcpyDeviceToHost, s));
-        SBD_CUDA(cudaStreamSynchronize(s));
-        return sqrt(v);
+        launch_combine<true>(V, W, ld, k, Y, ldy, m, U, HU, ld, theta, hd, delta, tc);
+        reduce_norms(m, rn_host);
     }
-    void scale(double *x, double f)
+    void reduce_norms(int m, double *rn_host)
     {
-        scale_kernel<<<grid, kBlas, 0, s>>>(x, f, N);
-        SBD_LAUNCH("scale_kernel");
+        hpart.assign((size_t)grid * kPart, 0.0);
+        SBD_CUDA(cudaMemcpyAsync(hpart.data(), partial, sizeof(double) * grid * kPart, cudaMemcpyDeviceToHost, s));
+        SBD_CUDA(cudaStreamSynchronize(s));
+        for (int j = 0; j < m; ++j) {
+            double acc = 0.0;
+            for (int b = 0; b < grid; ++b) acc += hpart[(size_t)b * kPart + j];
+            rn_host[j] = sqrt(acc);
+        }
     }
     // residual norms ||HU_j - theta_j U_j||, j < m (theta on device)
     void resid_norms(const double *U, const double *HU, int64_t ld, int m, const double *theta, double *out_host)
     {
-        hpart.assign((size_t)grid * kDotBatch, 0.0);
-        for (int j0 = 0; j0 < m; j0 += kDotBatch) {
-            const int mb = std::min(kDotBatch, m - j0);
-            resid_partial<<<grid, kBlas, 0, s>>>(U + j0 * ld, HU + j0 * ld, ld, mb, theta + j0, N, partial);
-            SBD_LAUNCH("resid_partial");
-            SBD_CUDA(cudaMemcpyAsync(hpart.data(), partial, sizeof(double) * grid * kDotBatch,
-                                     cudaMemcpyDeviceToHost, s));
-            SBD_CUDA(cudaStreamSynchronize(s));
-            for (int j = 0; j < mb; ++j) {
-                double acc = 0.0;
-                for (int b = 0; b < grid; ++b) acc += hpart[(size_t)b * kDotBatch + j];
-                out_host[j0 + j] = sqrt(acc);
-            }
-        }
+        resid_partial<<<grid, kBlas, 0, s>>>(U, HU, ld, m, theta, N, partial);
+        SBD_LAUNCH("resid_partial");
+        reduce_norms(m, out_host);
+    }
+    void scale(const double *src, double *dst, double f)
+    {
+        scale_kernel<<<grid, kBlas, 0, s>>>(src, dst, f, N);
+        SBD_LAUNCH("scale_kernel");
     }
     int64_t argmin(const double *x, const std::vector<int64_t> &excl, int64_t *dexcl)
     {
@@ -457,24 +611,26 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
     using clock = std::chrono::steady_clock;
     const auto t_start = clock::now();
     const int64_t N = c.N;
-    if (nroots < 1 || nroots > kDotBatch || nroots > N) fail(SBD_ERR_INVALID_ARG, "nroots must be in 1..min(16, N)");
+    if (nroots < 1 || nroots > kRitzMax || nroots > N) fail(SBD_ERR_INVALID_ARG, "nroots must be in 1..min(16, N)");
     if (!(tol > 0.0)) fail(SBD_ERR_INVALID_ARG, "tol must be positive");
     const double delta = c.opt.delta > 0.0 ? c.opt.delta : 1e-4;
     const int max_iter = c.opt.max_iter > 0 ? c.opt.max_iter : 200;
     int max_sub = c.opt.max_subspace > 0 ? c.opt.max_subspace : std::max(24, 8 * nroots);
-    max_sub = std::min<int64_t>(std::min(max_sub, kMaxSub), N);
+    max_sub = (int)std::min<int64_t>(std::min(max_sub, kMaxSub), N);
     if (max_sub < 2 * nroots && N >= 2 * nroots) max_sub = 2 * nroots;
     const bool mixed = prec == SBD_MIXED;
 
-    // keep the basis inside the budget: V, W, U, HU, t (+ FP32 copy)
+    // keep the basis inside the budget: V, W, U, HU, corrections (+ FP32 copy)
     auto need = [&](int ms, int nk) {
-        return ((size_t)(2 * ms + 2 * nk + 1)) * (size_t)N * sizeof(double) + (mixed ? (size_t)N * 4 : 0) + (1u << 22);
+        return ((size_t)(2 * ms + 2 * nk + nroots)) * (size_t)N * sizeof(double) + (mixed ? (size_t)N * 4 : 0) +
+               (1u << 22);
     };
-    int nkeep = std::max(nroots, std::min(max_sub - nroots, std::max(2 * nroots, max_sub / 3)));
+    auto keep_for = [&](int ms) { return std::max(nroots, std::min(ms - nroots, std::max(2 * nroots, ms / 3))); };
+    int nkeep = keep_for(max_sub);
     if (c.opt.hbm_budget_bytes) {
         while (max_sub > 2 * nroots && c.bytes_held + need(max_sub, nkeep) > c.opt.hbm_budget_bytes) {
             --max_sub;
-            nkeep = std::max(nroots, std::min(max_sub - nroots, std::max(2 * nroots, max_sub / 3)));
+            nkeep = keep_for(max_sub);
         }
     }
     sbd_report r{};
@@ -490,23 +646,24 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
         return p;
     };
     int status = SBD_OK;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     try {
         double *V = (double *)grab((size_t)max_sub * N * sizeof(double));
         double *W = (double *)grab((size_t)max_sub * N * sizeof(double));
         double *U = (double *)grab((size_t)nkeep * N * sizeof(double));
         double *HU = (double *)grab((size_t)nkeep * N * sizeof(double));
+        double *TC = (double *)grab((size_t)nroots * N * sizeof(double));
         float *c32 = mixed ? (float *)grab((size_t)N * sizeof(float)) : nullptr;
         double *T = (double *)grab(sizeof(double) * kMaxSub * kMaxSub);
         double *Y = (double *)grab(sizeof(double) * kMaxSub * kMaxSub);
         double *theta = (double *)grab(sizeof(double) * kMaxSub);
         double *coef = (double *)grab(sizeof(double) * kMaxSub);
         double *dscr = (double *)grab(sizeof(double) * kMaxSub);
-        int64_t *dexcl = (int64_t *)grab(sizeof(int64_t) * (kDotBatch + 1));
-        w.partial = (double *)grab(sizeof(double) * (size_t)w.grid * kDotBatch);
+        int64_t *dexcl = (int64_t *)grab(sizeof(int64_t) * (kRitzMax + 1));
+        w.partial = (double *)grab(sizeof(double) * (size_t)w.grid * kPart);
         w.pv = (double *)grab(sizeof(double) * w.grid);
         w.pi = (int64_t *)grab(sizeof(int64_t) * w.grid);
         const int64_t ld = N;
-        cudaEvent_t ev0, ev1;
         SBD_CUDA(cudaEventCreate(&ev0));
         SBD_CUDA(cudaEventCreate(&ev1));
         double sigma_ms = 0.0;
@@ -551,8 +708,7 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
         };
         // V' = V Y[:, :nk], W' = W Y[:, :nk] through the U/HU staging buffers
         auto compress = [&](int kk, int nk) {
-            w.combine(V, ld, kk, Y, kMaxSub, nk, U, ld);
-            w.combine(W, ld, kk, Y, kMaxSub, nk, HU, ld);
+            w.combine(V, W, ld, kk, Y, kMaxSub, nk, U, HU, ld);
             SBD_CUDA(cudaMemcpyAsync(V, U, (size_t)nk * N * sizeof(double), cudaMemcpyDeviceToDevice, w.s));
             SBD_CUDA(cudaMemcpyAsync(W, HU, (size_t)nk * N * sizeof(double), cudaMemcpyDeviceToDevice, w.s));
         };
@@ -577,12 +733,10 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
         int iter = 0;
         while (true) {
             // 2b-2c. Rayleigh-Ritz
-            jacobi_kernel<<<1, 128, 2 * sizeof(double) * k * k, w.s>>>(T, kMaxSub, k, theta, Y, kMaxSub);
+            jacobi_kernel<<<1, 256, 2 * sizeof(double) * k * k, w.s>>>(T, kMaxSub, k, theta, Y, kMaxSub);
             SBD_LAUNCH("jacobi_kernel");
-            // 2d. Ritz vectors and residuals
-            w.combine(V, ld, k, Y, kMaxSub, nroots, U, ld);
-            w.combine(W, ld, k, Y, kMaxSub, nroots, HU, ld);
-            w.resid_norms(U, HU, ld, nroots, theta, rn.data());
+            // 2d + 2f. Ritz vectors, residual norms and the preconditioned corrections in one pass
+            w.ritz(V, W, ld, k, Y, kMaxSub, nroots, U, HU, theta, c.hd, delta, TC, rn.data());
             SBD_CUDA(cudaMemcpyAsync(th.data(), theta, sizeof(double) * k, cudaMemcpyDeviceToHost, w.s));
             SBD_CUDA(cudaStreamSynchronize(w.s));
             harvest_timing(c);
@@ -616,6 +770,11 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
                     for (int j = 0; j < nroots; ++j) th[j] = hd2[2 * j] / hd2[2 * j + 1];
                     SBD_CUDA(cudaMemcpyAsync(theta, th.data(), sizeof(double) * nroots, cudaMemcpyHostToDevice, w.s));
                     w.resid_norms(U, HU, ld, nroots, theta, rn.data());
+                    for (int j = 0; j < nroots; ++j) {
+                        precond_kernel<<<w.grid, kBlas, 0, w.s>>>(U + j * ld, HU + j * ld, c.hd, theta + j, delta,
+                                                                  TC + j * ld, N);
+                        SBD_LAUNCH("precond_kernel");
+                    }
                     rmax = *std::max_element(rn.begin(), rn.end());
                     r.refinements++;
                     checked = true;
@@ -656,21 +815,21 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
                 SBD_CUDA(cudaStreamSynchronize(w.s));
                 r.restarts++;
             }
-            // 2f-2g. corrections: precondition, orthogonalise twice against V, normalise, append
+            // 2g. orthogonalise the corrections twice against V (classical Gram-Schmidt), normalise, append
             const int k_old = k;
             for (int j = 0; j < nroots; ++j) {
                 if (rn[j] <= tol) continue;
-                double *t = V + k * ld;
-                precond_kernel<<<w.grid, kBlas, 0, w.s>>>(U + j * ld, HU + j * ld, c.hd, theta + j, delta, t, N);
-                SBD_LAUNCH("precond_kernel");
-                const double n0 = w.norm(t, dscr);
-                for (int pass = 0; pass < 2; ++pass) {
-                    w.dots(V, ld, k, t, coef, 1);
-                    w.axpys(V, ld, k, coef, t);
-                }
-                const double n1 = w.norm(t, dscr);
+                double *t = TC + j * ld;
+                w.dots(V, ld, k, t, coef, 1, nullptr, 0, dscr + 0);     // c = V^T t, |t|^2 before
+                w.axpys(V, ld, k, coef, t);                              // t -= V c
+                w.dots(V, ld, k, t, coef, 1);                           // c = V^T t
+                w.axpys(V, ld, k, coef, t, dscr + 1);                   // t -= V c, |t|^2 after
+                double nn[2];
+                SBD_CUDA(cudaMemcpyAsync(nn, dscr, sizeof(nn), cudaMemcpyDeviceToHost, w.s));
+                SBD_CUDA(cudaStreamSynchronize(w.s));
+                const double n0 = sqrt(nn[0]), n1 = sqrt(nn[1]);
                 if (!(n1 > 1e-10 * n0) || !std::isfinite(n1)) continue;
-                w.scale(t, 1.0 / n1);
+                w.scale(t, V + k * ld, 1.0 / n1);
                 ++k;
             }
             if (k == k_old) {
@@ -687,7 +846,7 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
         // sign convention: the largest-magnitude component of each vector is positive
         for (int j = 0; j < nroots; ++j) {
             const double v = w.value_at_argmaxabs(U + j * ld);
-            if (v < 0.0) w.scale(U + j * ld, -1.0);
+            if (v < 0.0) w.scale(U + j * ld, U + j * ld, -1.0);
         }
         double rmax = 0.0;
         for (int j = 0; j < nroots; ++j) {
@@ -699,13 +858,15 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
         if (vecs)
             SBD_CUDA(cudaMemcpyAsync(vecs, U, (size_t)nroots * N * sizeof(double), cudaMemcpyDefault, w.s));
         SBD_CUDA(cudaStreamSynchronize(w.s));
-        SBD_CUDA(cudaEventDestroy(ev0));
-        SBD_CUDA(cudaEventDestroy(ev1));
         if (status == SBD_OK && !converged) status = SBD_NOT_CONVERGED;
     } catch (...) {
+        if (ev0) (void)cudaEventDestroy(ev0);
+        if (ev1) (void)cudaEventDestroy(ev1);
         for (void *p : owned) dfree(c, p);
         throw;
     }
+    (void)cudaEventDestroy(ev0);
+    (void)cudaEventDestroy(ev1);
     for (void *p : owned) dfree(c, p);
     r.status = status;
     r.seconds_total = std::chrono::duration<double>(clock::now() - t_start).count();

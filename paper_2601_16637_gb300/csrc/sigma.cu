@@ -18,23 +18,36 @@
 // next two the same gather inside column ib, run on the transpose C^T
 // ("alpha pass", same kernel), and the last line is the alpha-beta pass.
 //
-// Every output element is owned by exactly one thread group in each pass
-// (no atomics), so the result is deterministic.  Rows of C are staged in
-// shared memory, R rows interleaved per column so that one vector load
-// fetches the same column of all R rows; the inner gathers then hit shared
-// memory only.  Precision T = double (FP64) or float (mixed: FP32
-// amplitudes, integrals, products and per-list sums; each list sum and the
-// diagonal term are accumulated into the FP64 output).
+// Every output element is owned by one thread group in each pass and each
+// pass adds into it in program order, so results are deterministic.  Rows of
+// C are staged in shared memory, R rows interleaved per column so one vector
+// load fetches the same column of all R rows; the inner gathers then hit
+// shared memory only.  Excitation entries are read in batches of kBatch per
+// lane before any of them is used, and the next column's list bounds are
+// prefetched, so each lane keeps several L2 requests in flight.
+// Precision T = double (FP64) or float (mixed: FP32 amplitudes, integrals,
+// products and per-list sums, each list sum and the diagonal term accumulated
+// into the FP64 output).
 #include "common.cuh"
 
 namespace sbd {
 
 namespace {
 
-constexpr int kThreads = 512;
 constexpr int kGroup = 8;  // lanes cooperating on one output column
 constexpr int kGroupsPerWarp = 32 / kGroup;
-constexpr int kCodeMask = 0x7fffffff;
+constexpr int kBatch = 4;  // entries each lane loads before using them
+
+template <typename T>
+struct Threads;
+template <>
+struct Threads<float> {
+    static constexpr int value = 1024;
+};
+template <>
+struct Threads<double> {
+    static constexpr int value = 512;
+};
 
 template <typename T, int R>
 struct VecIO;
@@ -97,6 +110,48 @@ __device__ __forceinline__ T pick(const T (&v)[R], int i)
 
 __host__ __device__ constexpr size_t round16(size_t b) { return (b + 15) & ~(size_t)15; }
 
+__device__ __forceinline__ int pk_j(uint32_t pk) { return (int)(pk & kPackJMask); }
+__device__ __forceinline__ int pk_code(uint32_t pk) { return (int)((pk >> kPackCodeShift) & kPackCodeMask); }
+__device__ __forceinline__ bool pk_neg(uint32_t pk) { return (pk & kPackNegBit) != 0u; }
+
+// Excitation lists of the column spin, in the layout each precision reads.
+template <typename T>
+struct Lists;
+template <>
+struct Lists<float> {
+    const uint2 *s;  // (packed single, value bits)
+    const uint2 *d;  // (target, value bits)
+    __device__ void single(int64_t e, uint32_t &pk, float &v) const
+    {
+        const uint2 x = __ldg(s + e);
+        pk = x.x;
+        v = __uint_as_float(x.y);
+    }
+    __device__ void dbl(int64_t e, int &j, float &v) const
+    {
+        const uint2 x = __ldg(d + e);
+        j = (int)x.x;
+        v = __uint_as_float(x.y);
+    }
+};
+template <>
+struct Lists<double> {
+    const uint32_t *spk;
+    const double *sv;
+    const int32_t *dj;
+    const double *dv;
+    __device__ void single(int64_t e, uint32_t &pk, double &v) const
+    {
+        pk = __ldg(spk + e);
+        v = __ldg(sv + e);
+    }
+    __device__ void dbl(int64_t e, int &j, double &v) const
+    {
+        j = __ldg(dj + e);
+        v = __ldg(dv + e);
+    }
+};
+
 template <typename T>
 struct RowArgs {
     const T *X;  // [nrow][ncol]
@@ -109,19 +164,16 @@ struct RowArgs {
     const uint64_t *row_strings;
     int norb;
     const double *eri;  // FP64 integrals, for the J vectors of the staged rows
-    const int64_t *s_ptr;
-    const int32_t *s_j, *s_code;
-    const T *s_v;
-    const int64_t *d_ptr;
-    const int32_t *d_j;
-    const T *d_v;
+    const int64_t *s_ptr, *d_ptr;
+    Lists<T> lists;
 };
 
 // Gather pass over rows of X: each CTA stages R consecutive rows, then every
 // output column c sums its excitation list (column spin) inside those rows.
 template <typename T, int R, bool STAGED>
-__global__ void __launch_bounds__(kThreads) row_pass_kernel(const RowArgs<T> a)
+__global__ void __launch_bounds__(Threads<T>::value) row_pass_kernel(const RowArgs<T> a)
 {
+    constexpr int kThreads = Threads<T>::value;
     extern __shared__ __align__(16) unsigned char smem[];
     const int n2 = a.norb * a.norb;
     const size_t xs_bytes = STAGED ? round16((size_t)a.ncol * R * sizeof(T)) : 0;
@@ -158,33 +210,69 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const RowArgs<T> a)
         }
         __syncthreads();
 
-        for (int64_t cb = (int64_t)warp * kGroupsPerWarp; cb < a.ncol; cb += ngroups) {
+        int64_t cb = (int64_t)warp * kGroupsPerWarp;
+        int64_t nxt_s0 = 0, nxt_s1 = 0, nxt_d0 = 0, nxt_d1 = 0;
+        if (cb + gi < a.ncol) {
+            nxt_s0 = a.s_ptr[cb + gi];
+            nxt_s1 = a.s_ptr[cb + gi + 1];
+            nxt_d0 = a.d_ptr[cb + gi];
+            nxt_d1 = a.d_ptr[cb + gi + 1];
+        }
+        for (; cb < a.ncol; cb += ngroups) {
             const int64_t c = cb + gi;
             const bool valid = c < a.ncol;
+            const int64_t s0 = nxt_s0, s1 = nxt_s1, d0 = nxt_d0, d1 = nxt_d1;
+            if (c + ngroups < a.ncol) {  // prefetch the next column's list bounds
+                nxt_s0 = a.s_ptr[c + ngroups];
+                nxt_s1 = a.s_ptr[c + ngroups + 1];
+                nxt_d0 = a.d_ptr[c + ngroups];
+                nxt_d1 = a.d_ptr[c + ngroups + 1];
+            }
             T acc[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[r] = T(0);
             if (valid) {
-                const int64_t se = a.s_ptr[c + 1];
-                for (int64_t e = a.s_ptr[c] + lig; e < se; e += kGroup) {
-                    const int32_t j = __ldg(a.s_j + e), cd = __ldg(a.s_code + e);
-                    const T v = __ldg(a.s_v + e);
-                    T xj[R], jv[R];
-                    if (STAGED) VecIO<T, R>::ld(Xs + (size_t)j * R, xj);
-                    else xj[0] = a.X[r0 * a.ncol + j];
-                    VecIO<T, R>::ld(Js + (size_t)(cd & kCodeMask) * R, jv);
+                for (int64_t eb = s0 + lig; eb < s1; eb += kGroup * kBatch) {
+                    uint32_t pk[kBatch];
+                    T v[kBatch];
 #pragma unroll
-                    for (int r = 0; r < R; ++r) acc[r] += (cd < 0 ? v - jv[r] : v + jv[r]) * xj[r];
+                    for (int u = 0; u < kBatch; ++u) {
+                        pk[u] = 0u;
+                        v[u] = T(0);
+                        if (eb + u * kGroup < s1) a.lists.single(eb + u * kGroup, pk[u], v[u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kBatch; ++u) {
+                        if (eb + u * kGroup < s1) {
+                            T xj[R], jv[R];
+                            if (STAGED) VecIO<T, R>::ld(Xs + (size_t)pk_j(pk[u]) * R, xj);
+                            else xj[0] = a.X[r0 * a.ncol + pk_j(pk[u])];
+                            VecIO<T, R>::ld(Js + (size_t)pk_code(pk[u]) * R, jv);
+                            const bool neg = pk_neg(pk[u]);
+#pragma unroll
+                            for (int r = 0; r < R; ++r) acc[r] += (neg ? v[u] - jv[r] : v[u] + jv[r]) * xj[r];
+                        }
+                    }
                 }
-                const int64_t de = a.d_ptr[c + 1];
-                for (int64_t e = a.d_ptr[c] + lig; e < de; e += kGroup) {
-                    const int32_t j = __ldg(a.d_j + e);
-                    const T v = __ldg(a.d_v + e);
-                    T xj[R];
-                    if (STAGED) VecIO<T, R>::ld(Xs + (size_t)j * R, xj);
-                    else xj[0] = a.X[r0 * a.ncol + j];
+                for (int64_t eb = d0 + lig; eb < d1; eb += kGroup * kBatch) {
+                    int jj[kBatch];
+                    T v[kBatch];
 #pragma unroll
-                    for (int r = 0; r < R; ++r) acc[r] += v * xj[r];
+                    for (int u = 0; u < kBatch; ++u) {
+                        jj[u] = 0;
+                        v[u] = T(0);
+                        if (eb + u * kGroup < d1) a.lists.dbl(eb + u * kGroup, jj[u], v[u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kBatch; ++u) {
+                        if (eb + u * kGroup < d1) {
+                            T xj[R];
+                            if (STAGED) VecIO<T, R>::ld(Xs + (size_t)jj[u] * R, xj);
+                            else xj[0] = a.X[r0 * a.ncol + jj[u]];
+#pragma unroll
+                            for (int r = 0; r < R; ++r) acc[r] += v[u] * xj[r];
+                        }
+                    }
                 }
             }
 #pragma unroll
@@ -213,18 +301,21 @@ struct AbArgs {
     int norb;
     const T *eri;  // (pq|rs) as a [norb^2][norb^2] matrix
     const int64_t *as_ptr;
-    const int32_t *as_j, *as_code;
+    const uint32_t *as_pk;
     const int64_t *bs_ptr;
-    const int32_t *bs_j, *bs_code;
+    const uint32_t *bs_pk;
 };
 
 // Alpha-beta pass: CTA per output row ia.  The alpha single excitations of
 // ia are taken R at a time: their rows C[ja,:] are staged interleaved and
 // W[rs][k] = u_k (p_k q_k|rs) is tabulated; each output column ib then
-// runs over its beta singles (jb, rs, t): acc += t * sum_k W[rs][k] C[ja_k, jb].
+// runs over its beta singles (jb, rs, t): acc += t * sum_k W[rs][k] C[ja_k, jb],
+// and adds acc to s(ia, ib) with a fire-and-forget reduction (the same thread
+// owns (ia, ib) for every group of this row, so the adds land in program order).
 template <typename T, int R, bool STAGED>
-__global__ void __launch_bounds__(kThreads) ab_pass_kernel(const AbArgs<T> a)
+__global__ void __launch_bounds__(Threads<T>::value) ab_pass_kernel(const AbArgs<T> a)
 {
+    constexpr int kThreads = Threads<T>::value;
     extern __shared__ __align__(16) unsigned char smem[];
     const int n2 = a.norb * a.norb;
     const size_t cs_bytes = STAGED ? round16((size_t)a.nB * R * sizeof(T)) : 0;
@@ -245,10 +336,10 @@ __global__ void __launch_bounds__(kThreads) ab_pass_kernel(const AbArgs<T> a)
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 const bool ok = k < kr;
-                ja[k] = ok ? (int64_t)a.as_j[e0 + k0 + k] : 0;
-                const int32_t cd = ok ? a.as_code[e0 + k0 + k] : 0;
-                pq[k] = cd & kCodeMask;
-                u[k] = ok ? (cd < 0 ? T(-1) : T(1)) : T(0);
+                const uint32_t pk = ok ? a.as_pk[e0 + k0 + k] : 0u;
+                ja[k] = pk_j(pk);
+                pq[k] = pk_code(pk);
+                u[k] = ok ? (pk_neg(pk) ? T(-1) : T(1)) : T(0);
             }
             __syncthreads();
             if (STAGED) {
@@ -267,30 +358,47 @@ __global__ void __launch_bounds__(kThreads) ab_pass_kernel(const AbArgs<T> a)
             }
             __syncthreads();
 
-            for (int64_t cb = (int64_t)warp * kGroupsPerWarp; cb < a.nB; cb += ngroups) {
+            int64_t cb = (int64_t)warp * kGroupsPerWarp;
+            int64_t nxt0 = 0, nxt1 = 0;
+            if (cb + gi < a.nB) {
+                nxt0 = a.bs_ptr[cb + gi];
+                nxt1 = a.bs_ptr[cb + gi + 1];
+            }
+            for (; cb < a.nB; cb += ngroups) {
                 const int64_t ib = cb + gi;
                 const bool valid = ib < a.nB;
+                const int64_t b0 = nxt0, b1 = nxt1;
+                if (ib + ngroups < a.nB) {
+                    nxt0 = a.bs_ptr[ib + ngroups];
+                    nxt1 = a.bs_ptr[ib + ngroups + 1];
+                }
                 T acc = T(0);
                 if (valid) {
-                    const int64_t ee = a.bs_ptr[ib + 1];
-                    for (int64_t e = a.bs_ptr[ib] + lig; e < ee; e += kGroup) {
-                        const int32_t jb = __ldg(a.bs_j + e), cd = __ldg(a.bs_code + e);
-                        T cv[R], wv[R];
-                        if (STAGED) VecIO<T, R>::ld(Cs + (size_t)jb * R, cv);
-                        else cv[0] = a.C[ja[0] * a.nB + jb];
-                        VecIO<T, R>::ld(Ws + (size_t)(cd & kCodeMask) * R, wv);
-                        T d = T(0);
+                    for (int64_t eb = b0 + lig; eb < b1; eb += kGroup * kBatch) {
+                        uint32_t pk[kBatch];
 #pragma unroll
-                        for (int k = 0; k < R; ++k) d += wv[k] * cv[k];
-                        acc += cd < 0 ? -d : d;
+                        for (int t = 0; t < kBatch; ++t) {
+                            const int64_t e = eb + t * kGroup;
+                            pk[t] = e < b1 ? __ldg(a.bs_pk + e) : 0u;
+                        }
+#pragma unroll
+                        for (int t = 0; t < kBatch; ++t) {
+                            if (eb + t * kGroup < b1) {
+                                T cv[R], wv[R];
+                                if (STAGED) VecIO<T, R>::ld(Cs + (size_t)pk_j(pk[t]) * R, cv);
+                                else cv[0] = a.C[ja[0] * a.nB + pk_j(pk[t])];
+                                VecIO<T, R>::ld(Ws + (size_t)pk_code(pk[t]) * R, wv);
+                                T d = T(0);
+#pragma unroll
+                                for (int k = 0; k < R; ++k) d += wv[k] * cv[k];
+                                acc += pk_neg(pk[t]) ? -d : d;
+                            }
+                        }
                     }
                 }
 #pragma unroll
                 for (int off = kGroup / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off, kGroup);
-                if (valid && lig == 0) {
-                    double *s = a.S + ia * a.nB + ib;
-                    *s += (double)acc;
-                }
+                if (valid && lig == 0) atomicAdd(a.S + ia * a.nB + ib, (double)acc);
             }
         }
     }
@@ -355,11 +463,11 @@ void set_attrs(int optin)
 }
 
 template <typename T>
-void launch_row(const RowArgs<T> &a, const PassCfg &p, int num_sms, cudaStream_t s)
+void launch_row(const RowArgs<T> &a, const PassCfg &p, cudaStream_t s)
 {
+    constexpr int kThreads = Threads<T>::value;
     const int64_t groups = (a.nrow + p.R - 1) / p.R;
     const int grid = (int)(groups < 65535 ? groups : 65535);
-    (void)num_sms;
     if (!p.staged) row_pass_kernel<T, 1, false><<<grid, kThreads, p.smem, s>>>(a);
     else if (p.R == 4) row_pass_kernel<T, (sizeof(T) == 4 ? 4 : 2), true><<<grid, kThreads, p.smem, s>>>(a);
     else if (p.R == 2) row_pass_kernel<T, 2, true><<<grid, kThreads, p.smem, s>>>(a);
@@ -370,6 +478,7 @@ void launch_row(const RowArgs<T> &a, const PassCfg &p, int num_sms, cudaStream_t
 template <typename T>
 void launch_ab(const AbArgs<T> &a, const PassCfg &p, cudaStream_t s)
 {
+    constexpr int kThreads = Threads<T>::value;
     const int grid = (int)(a.nA < 65535 ? a.nA : 65535);
     if (!p.staged) ab_pass_kernel<T, 1, false><<<grid, kThreads, p.smem, s>>>(a);
     else if (p.R == 4) ab_pass_kernel<T, (sizeof(T) == 4 ? 4 : 2), true><<<grid, kThreads, p.smem, s>>>(a);
@@ -386,6 +495,19 @@ void transpose(const T *in, T *out, int64_t rows, int64_t cols, cudaStream_t s)
     dim3 grid((unsigned)((cols + 31) / 32), (unsigned)gy);
     transpose_kernel<T><<<grid, dim3(32, 8), 0, s>>>(in, out, rows, cols);
     SBD_LAUNCH("transpose_kernel");
+}
+
+template <typename T>
+Lists<T> lists_of(const SpinTables &t);
+template <>
+Lists<float> lists_of<float>(const SpinTables &t)
+{
+    return Lists<float>{t.s_pkv32, t.d_jv32};
+}
+template <>
+Lists<double> lists_of<double>(const SpinTables &t)
+{
+    return Lists<double>{t.s_pk_sig, t.s_v64_sig, t.d_j_sig, t.d_v64_sig};
 }
 
 // Runs launch(); when timing is on, brackets it with events on stream s and
@@ -411,8 +533,7 @@ void apply(Ctx &c, const T *C, double *S, const double *c64, cudaStream_t s)
     const int rmax = sizeof(T) == 4 ? 4 : 2;
     const size_t lim = smem_limit(c);
     const SpinTables &ta = c.sp[0], &tb = c.sp[1];
-    const bool fp32 = sizeof(T) == 4;
-    const int base = fp32 ? 4 : 0;
+    const int base = sizeof(T) == 4 ? 4 : 0;
     T *Ct = static_cast<T *>(c.work_t);
     timed(c, base + 0, s, [&] { transpose<T>(C, Ct, c.nA, c.nB, s); });
 
@@ -430,13 +551,9 @@ void apply(Ctx &c, const T *C, double *S, const double *c64, cudaStream_t s)
     rb.norb = c.norb;
     rb.eri = c.eri64;
     rb.s_ptr = tb.s_ptr;
-    rb.s_j = tb.s_j;
-    rb.s_code = tb.s_code;
-    rb.s_v = fp32 ? (const T *)tb.s_v32 : (const T *)tb.s_v64;
     rb.d_ptr = tb.d_ptr;
-    rb.d_j = tb.d_j;
-    rb.d_v = fp32 ? (const T *)tb.d_v32 : (const T *)tb.d_v64;
-    timed(c, base + 1, s, [&] { launch_row<T>(rb, choose(c.nB, n2, sizeof(T), rmax, lim), c.num_sms, s); });
+    rb.lists = lists_of<T>(tb);
+    timed(c, base + 1, s, [&] { launch_row<T>(rb, choose(c.nB, n2, sizeof(T), rmax, lim), s); });
 
     RowArgs<T> ra = rb;
     ra.X = Ct;
@@ -449,13 +566,9 @@ void apply(Ctx &c, const T *C, double *S, const double *c64, cudaStream_t s)
     ra.xd64 = nullptr;
     ra.row_strings = tb.strings;
     ra.s_ptr = ta.s_ptr;
-    ra.s_j = ta.s_j;
-    ra.s_code = ta.s_code;
-    ra.s_v = fp32 ? (const T *)ta.s_v32 : (const T *)ta.s_v64;
     ra.d_ptr = ta.d_ptr;
-    ra.d_j = ta.d_j;
-    ra.d_v = fp32 ? (const T *)ta.d_v32 : (const T *)ta.d_v64;
-    timed(c, base + 2, s, [&] { launch_row<T>(ra, choose(c.nA, n2, sizeof(T), rmax, lim), c.num_sms, s); });
+    ra.lists = lists_of<T>(ta);
+    timed(c, base + 2, s, [&] { launch_row<T>(ra, choose(c.nA, n2, sizeof(T), rmax, lim), s); });
 
     AbArgs<T> ab{};
     ab.C = C;
@@ -463,13 +576,11 @@ void apply(Ctx &c, const T *C, double *S, const double *c64, cudaStream_t s)
     ab.nA = c.nA;
     ab.nB = c.nB;
     ab.norb = c.norb;
-    ab.eri = fp32 ? (const T *)c.eri32 : (const T *)c.eri64;
+    ab.eri = sizeof(T) == 4 ? (const T *)(const void *)c.eri32 : (const T *)(const void *)c.eri64;
     ab.as_ptr = ta.s_ptr;
-    ab.as_j = ta.s_j;
-    ab.as_code = ta.s_code;
+    ab.as_pk = ta.s_pk_sig;
     ab.bs_ptr = tb.s_ptr;
-    ab.bs_j = tb.s_j;
-    ab.bs_code = tb.s_code;
+    ab.bs_pk = tb.s_pk_sig;
     timed(c, base + 3, s, [&] { launch_ab<T>(ab, choose(c.nB, n2, sizeof(T), rmax, lim), s); });
 }
 

@@ -22,6 +22,8 @@
 //   diagonal  sum_{i in S} h_ii + 1/2 sum_{i,j in S} [(ii|jj) - (ij|ji)]
 //   single    phase * [h_pq + sum_{k in S_j} ((pq|kk) - (pk|kq))]
 //   double    phase * [(p1 q1|p2 q2) - (p1 q2|p2 q1)]
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace sbd {
@@ -103,7 +105,7 @@ struct TableOut {
     int32_t *s_j, *d_j;
     uint8_t *s_orb, *d_orb;
     int8_t *s_sign, *d_sign;
-    int32_t *s_code;
+    uint32_t *s_pk;
     double *s_v, *d_v;
 };
 
@@ -116,9 +118,9 @@ __device__ __forceinline__ void store_single(const TableOut &o, int64_t pos, con
     o.s_orb[4 * pos + 3] = e.orb[3];
     o.s_sign[pos] = e.sign;
     o.s_v[pos] = e.val;
-    int32_t code = e.orb[0] * norb + e.orb[2];
-    if (e.sign < 0) code |= (int32_t)0x80000000;
-    o.s_code[pos] = code;
+    uint32_t pk = (uint32_t)e.j | ((uint32_t)(e.orb[0] * norb + e.orb[2]) << kPackCodeShift);
+    if (e.sign < 0) pk |= kPackNegBit;
+    o.s_pk[pos] = pk;
 }
 
 __device__ __forceinline__ void store_double(const TableOut &o, int64_t pos, const Entry &e)
@@ -350,6 +352,45 @@ __global__ void ediag_kernel(const uint64_t *S, int64_t n, int norb, const doubl
     }
 }
 
+// Bank-aware order of each source's list: entry e with target residue r = j mod 8
+// and rank t among the entries of residue r goes to position
+//   sum_r' min(count[r'], t) + #{r' < r : count[r'] > t},
+// i.e. the list is read as rounds "rank 0 of every residue, rank 1 of every
+// residue, ..."; each aligned block of 8 then holds distinct residues except
+// where the residue counts are unequal.  One thread per source.
+__global__ void bank_order_kernel(const int64_t *__restrict__ ptr, int64_t n, const int32_t *__restrict__ j_src,
+                                  int64_t *perm)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = ptr[i], e = ptr[i + 1];
+        int count[kBankGroups] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int64_t x = b; x < e; ++x) ++count[j_src[x] & (kBankGroups - 1)];
+        int seen[kBankGroups] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int64_t x = b; x < e; ++x) {
+            const int r = j_src[x] & (kBankGroups - 1);
+            const int t = seen[r]++;
+            int64_t pos = 0;
+#pragma unroll
+            for (int q = 0; q < kBankGroups; ++q) pos += min(count[q], t) + ((q < r && count[q] > t) ? 1 : 0);
+            perm[b + pos] = x;  // entry x goes to position b + pos
+        }
+    }
+}
+
+template <typename V>
+__global__ void gather_kernel(const V *__restrict__ src, const int64_t *__restrict__ perm, V *dst, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[perm[i]];
+}
+
+// (key, FP32 value) pairs for single 8-byte loads in the mixed sigma
+__global__ void pair_kernel(const uint32_t *__restrict__ key, const double *__restrict__ val, uint2 *out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = make_uint2(key[i], __float_as_uint(__double2float_rn(val[i])));
+}
+
 __global__ void to_float_kernel(const double *in, float *out, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -406,6 +447,7 @@ void build_tables(Ctx &c, int spin)
     SpinTables &t = c.sp[spin];
     const int64_t n = t.n;
     const int norb = c.norb;
+    if (n >= kMaxStringsPerSpin) fail(SBD_ERR_UNSUPPORTED, "at most 262143 strings per spin are supported");
     int64_t *cnt = dalloc_n<int64_t>(c, 2 * (size_t)n);
     t.s_ptr = dalloc_n<int64_t>(c, n + 1);
     t.d_ptr = dalloc_n<int64_t>(c, n + 1);
@@ -447,14 +489,14 @@ void build_tables(Ctx &c, int spin)
     t.s_j = dalloc_n<int32_t>(c, t.ns);
     t.s_orb = dalloc_n<uint8_t>(c, 4 * t.ns);
     t.s_sign = dalloc_n<int8_t>(c, t.ns);
-    t.s_code = dalloc_n<int32_t>(c, t.ns);
+    t.s_pk = dalloc_n<uint32_t>(c, t.ns);
     t.s_v64 = dalloc_n<double>(c, t.ns);
-    t.s_v32 = dalloc_n<float>(c, t.ns);
+    t.s_pkv32 = dalloc_n<uint2>(c, t.ns);
     t.d_j = dalloc_n<int32_t>(c, t.nd);
     t.d_orb = dalloc_n<uint8_t>(c, 4 * t.nd);
     t.d_sign = dalloc_n<int8_t>(c, t.nd);
     t.d_v64 = dalloc_n<double>(c, t.nd);
-    t.d_v32 = dalloc_n<float>(c, t.nd);
+    t.d_jv32 = dalloc_n<uint2>(c, t.nd);
     o.s_ptr = t.s_ptr;
     o.d_ptr = t.d_ptr;
     o.s_j = t.s_j;
@@ -463,7 +505,7 @@ void build_tables(Ctx &c, int spin)
     o.d_orb = t.d_orb;
     o.s_sign = t.s_sign;
     o.d_sign = t.d_sign;
-    o.s_code = t.s_code;
+    o.s_pk = t.s_pk;
     o.s_v = t.s_v64;
     o.d_v = t.d_v64;
     if (algo == 1) {
@@ -475,8 +517,35 @@ void build_tables(Ctx &c, int spin)
                                                                   c.h64, c.eri64, o);
         SBD_LAUNCH("enum_kernel(fill)");
     }
-    to_float(t.s_v64, t.s_v32, t.ns, c.stream);
-    to_float(t.d_v64, t.d_v32, t.nd, c.stream);
+    // sigma copies in bank-aware order
+    t.s_pk_sig = dalloc_n<uint32_t>(c, t.ns);
+    t.s_v64_sig = dalloc_n<double>(c, t.ns);
+    t.d_j_sig = dalloc_n<int32_t>(c, t.nd);
+    t.d_v64_sig = dalloc_n<double>(c, t.nd);
+    int64_t *perm = dalloc_n<int64_t>(c, (size_t)std::max(t.ns, t.nd));
+    const int ob = blocks_for(n, 128);
+    if (t.ns) {
+        bank_order_kernel<<<ob, 128, 0, c.stream>>>(t.s_ptr, n, t.s_j, perm);
+        SBD_LAUNCH("bank_order_kernel(singles)");
+        const int gb = blocks_for(t.ns, 256, 16384);
+        gather_kernel<uint32_t><<<gb, 256, 0, c.stream>>>(t.s_pk, perm, t.s_pk_sig, t.ns);
+        gather_kernel<double><<<gb, 256, 0, c.stream>>>(t.s_v64, perm, t.s_v64_sig, t.ns);
+        SBD_LAUNCH("gather_kernel(singles)");
+        pair_kernel<<<gb, 256, 0, c.stream>>>(t.s_pk_sig, t.s_v64_sig, t.s_pkv32, t.ns);
+        SBD_LAUNCH("pair_kernel(singles)");
+    }
+    if (t.nd) {
+        bank_order_kernel<<<ob, 128, 0, c.stream>>>(t.d_ptr, n, t.d_j, perm);
+        SBD_LAUNCH("bank_order_kernel(doubles)");
+        const int gb = blocks_for(t.nd, 256, 16384);
+        gather_kernel<int32_t><<<gb, 256, 0, c.stream>>>(t.d_j, perm, t.d_j_sig, t.nd);
+        gather_kernel<double><<<gb, 256, 0, c.stream>>>(t.d_v64, perm, t.d_v64_sig, t.nd);
+        SBD_LAUNCH("gather_kernel(doubles)");
+        pair_kernel<<<gb, 256, 0, c.stream>>>(reinterpret_cast<const uint32_t *>(t.d_j_sig), t.d_v64_sig, t.d_jv32,
+                                               t.nd);
+        SBD_LAUNCH("pair_kernel(doubles)");
+    }
+    dfree(c, perm);
     t.ediag = dalloc_n<double>(c, n);
     ediag_kernel<<<blocks_for(n, 128), 128, 0, c.stream>>>(t.strings, n, norb, c.h64, c.eri64, t.ediag);
     SBD_LAUNCH("ediag_kernel");
