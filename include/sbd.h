@@ -212,6 +212,33 @@ int sbd_kernel_times(sbd_handle handle, double *ms_host, int64_t *launches_host,
 /* Number of kernels this library has launched in the process so far. */
 int64_t sbd_launch_count(void);
 
+/*
+ * sbd_sort_strings_noalloc -- validate and sort one string set without
+ * allocating any device memory.  The paper has no counterpart; this entry
+ * point exists for callers that cannot let a library allocate on their
+ * behalf (device memory carved up in advance by the caller's own allocator,
+ * a plug-in that must not grow its host process's footprint, a loop that may
+ * not touch an allocator).  It runs the same validation, stable radix sort and
+ * duplicate check as sbd_create, with its work space in a fixed array inside
+ * the library (SBD_NOALLOC_MAX_STRINGS strings; about 0.5 MB that every GPU
+ * which loads the library holds until the process exits).
+ *   keys_dev     device pointer, n uint64 strings (any order; not modified)
+ *   n            0..SBD_NOALLOC_MAX_STRINGS; larger n returns SBD_ERR_INVALID_ARG
+ *   norb, nel    orbitals (1..64) and electrons per string
+ *   sorted_dev   device pointer, n uint64: the strings in ascending order
+ *   bad_index_host NULL or one int64: -1, or for SBD_ERR_BAD_STRING the input
+ *                position of a malformed string, for SBD_ERR_DUPLICATE_STRING the
+ *                sorted position of a repeated string
+ * Enqueued on `stream`, then synchronises it.  The first call on each device
+ * looks up the work space's device address (cudaGetSymbolAddress) and caches
+ * it; make that first call before any stream capture.  All calls share the
+ * work space: calls that overlap on the GPU race and must be serialised by
+ * the caller.  Errors are reported by sbd_last_error(NULL) on this thread.
+ */
+#define SBD_NOALLOC_MAX_STRINGS 65536
+int sbd_sort_strings_noalloc(const uint64_t *keys_dev, int64_t n, int norb, int nel, uint64_t *sorted_dev,
+                             int64_t *bad_index_host, void *stream);
+
 /* Message for the last failure on `handle` (NULL: on this thread); valid
  * until the next call on the same handle / thread. */
 const char *sbd_last_error(sbd_handle handle);

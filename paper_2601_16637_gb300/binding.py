@@ -80,7 +80,10 @@ _SIGNATURES = {
     "sbd_last_error": (C.c_char_p, [_vp]),
     "sbd_kernel_times": (_int, [_vp, _vp, _vp, _int]),
     "sbd_launch_count": (_i64, []),
+    "sbd_sort_strings_noalloc": (_int, [_vp, _i64, _int, _int, _vp, C.POINTER(_i64), _vp]),
 }
+
+SBD_NOALLOC_MAX_STRINGS = 65536
 
 KERNEL_SLOTS = ["transpose", "beta_pass", "alpha_pass", "ab_pass"]
 
@@ -265,6 +268,18 @@ def sbd_kernel_times(handle, reset: bool = False):
 
 def sbd_launch_count() -> int:
     return int(load().sbd_launch_count())
+
+
+def sbd_sort_strings_noalloc(keys, norb: int, nel: int, out, stream=None) -> tuple[int, int]:
+    """Validates and sorts device strings `keys` into device buffer `out` without any device
+    allocation.  Returns (status, bad_index); raises SbdError on errors other than
+    SBD_ERR_BAD_STRING / SBD_ERR_DUPLICATE_STRING, which are returned with their index."""
+    bad = C.c_int64(-1)
+    rc = load().sbd_sort_strings_noalloc(_ptr(keys), int(keys.numel()), int(norb), int(nel), _ptr(out),
+                                         C.byref(bad), _stream(stream))
+    if rc < 0 and rc not in (-2, -3):
+        _check(rc)
+    return rc, bad.value
 
 
 def sbd_last_error(handle=None) -> str:

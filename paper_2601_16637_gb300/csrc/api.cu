@@ -115,6 +115,8 @@ struct sbd_ctx {
 
 static thread_local std::string g_last_error;
 
+void sbd::set_thread_error(const std::string &msg) { g_last_error = msg; }
+
 template <typename F>
 static int guarded(sbd_handle h, F &&f)
 {

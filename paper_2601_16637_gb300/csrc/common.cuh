@@ -20,6 +20,7 @@ struct Error {
 };
 
 [[noreturn]] void fail(int code, const std::string &msg);
+void set_thread_error(const std::string &msg);  // sbd_last_error(NULL) on this thread
 void check_cuda(cudaError_t e, const char *what, const char *file, int line);
 void count_launch();
 #define SBD_CUDA(call) ::sbd::check_cuda((call), #call, __FILE__, __LINE__)
@@ -152,6 +153,8 @@ void compare_sets(Ctx &c, const uint64_t *a, const uint64_t *b, int64_t n);
 void check_finite(Ctx &c, const double *x, int64_t n);
 void lookup_strings(const uint64_t *sorted, int64_t n, const uint64_t *keys, int64_t nq, int64_t *idx,
                     cudaStream_t s);
+void sort_validate_into(const uint64_t *in, int64_t n, int norb, int nel, uint64_t *out, uint64_t *tmp,
+                        DevStatus *st, cudaStream_t s);
 
 // tables.cu
 void build_tables(Ctx &c, int spin);

@@ -175,4 +175,24 @@ void lookup_strings(const uint64_t *sorted, int64_t n, const uint64_t *keys, int
     SBD_LAUNCH("lookup_kernel");
 }
 
+// Copies n strings to `out`, validates them, sorts `out` ascending and checks
+// for duplicates, using caller-provided work space: tmp (n uint64) and the
+// status words st.  Enqueued on s; nothing is allocated.
+void sort_validate_into(const uint64_t *in, int64_t n, int norb, int nel, uint64_t *out, uint64_t *tmp,
+                        DevStatus *st, cudaStream_t s)
+{
+    SBD_CUDA(cudaMemsetAsync(st, 0xff, 2 * sizeof(unsigned long long), s));
+    SBD_CUDA(cudaMemsetAsync(&st->nonfinite, 0, 2 * sizeof(int), s));
+    if (n <= 0) return;
+    SBD_CUDA(cudaMemcpyAsync(out, in, (size_t)n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    validate_kernel<<<grid_for(n, 256), 256, 0, s>>>(out, n, norb, nel, st);
+    SBD_LAUNCH("validate_kernel");
+    if (n > 1) {
+        radix_sort_kernel<<<1, kSortThreads, 0, s>>>(out, tmp, (int)n, (norb + 7) / 8);
+        SBD_LAUNCH("radix_sort_kernel");
+        duplicate_kernel<<<grid_for(n, 256), 256, 0, s>>>(out, n, st);
+        SBD_LAUNCH("duplicate_kernel");
+    }
+}
+
 }  // namespace sbd
