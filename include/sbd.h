@@ -89,6 +89,7 @@ typedef struct {
     int sigma_mixed;      /* vectors multiplied by the mixed sigma */
     int restarts;         /* subspace restarts */
     int refinements;      /* FP64 defect-correction steps (mixed mode) */
+    int reorthogonalisations; /* second Gram-Schmidt passes (taken when the first removed > 1/sqrt(2)) */
     int status;           /* same as the return value */
     double max_residual;  /* largest final residual norm (FP64-evaluated) */
     double seconds_total; /* wall time inside sbd_davidson */

@@ -43,7 +43,8 @@ class sbd_options(C.Structure):
 
 class sbd_report(C.Structure):
     _fields_ = [("iterations", C.c_int), ("sigma_fp64", C.c_int), ("sigma_mixed", C.c_int),
-                ("restarts", C.c_int), ("refinements", C.c_int), ("status", C.c_int),
+                ("restarts", C.c_int), ("refinements", C.c_int), ("reorthogonalisations", C.c_int),
+                ("status", C.c_int),
                 ("max_residual", C.c_double), ("seconds_total", C.c_double), ("seconds_sigma", C.c_double)]
 
     def as_dict(self) -> dict:

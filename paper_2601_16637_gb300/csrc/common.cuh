@@ -26,14 +26,16 @@ void count_launch();
 #define SBD_CUDA(call) ::sbd::check_cuda((call), #call, __FILE__, __LINE__)
 #define SBD_LAUNCH(what) (::sbd::count_launch(), ::sbd::check_cuda(cudaGetLastError(), what, __FILE__, __LINE__))
 
-// packed single-excitation entries: strings per spin must stay below 2^18
+// Packed single-excitation entry: target j in bits 0-17, phase -1 in bit 18, code p*norb+q in
+// bits 19-30, so pk >> 18 = 2*code + (phase < 0) indexes sign-folded coefficient tables.  A
+// single always has p != q, so code 0 never occurs: pk = 0 is the padding entry, and the
+// coefficient-table rows of code 0 are kept zero.  Strings per spin must stay below 2^18.
 constexpr int kPackJBits = 18;
 constexpr uint32_t kPackJMask = (1u << kPackJBits) - 1u;
-constexpr int kPackCodeShift = 18;
-constexpr uint32_t kPackCodeMask = 0xfffu;
-constexpr uint32_t kPackNegBit = 1u << 30;
+constexpr int kPackKeyShift = 18;  // pk >> 18 = 2*code + neg
 constexpr int64_t kMaxStringsPerSpin = (int64_t)1 << kPackJBits;
-constexpr int kBankGroups = 8;  // 16-byte bank groups of shared memory (32 banks x 4 bytes)
+constexpr int kBankGroups = 8;     // 16-byte bank groups of shared memory (32 banks x 4 bytes)
+constexpr int kListPad = 4;        // sigma lists are padded to multiples of 4 entries (16-byte loads)
 
 // ---------------------------------------------------------------------------
 // device status words written by validation kernels
@@ -61,9 +63,11 @@ struct SpinTables {
     // packed single: target j (bits 0-17) | code p*norb+q (bits 18-29) | phase -1 (bit 30)
     uint32_t *s_pk = nullptr;
     double *s_v64 = nullptr, *d_v64 = nullptr;   // same-spin matrix elements
-    // Sigma copies of the lists: the same entries per source, reordered so that every aligned
-    // block of 8 entries has distinct targets modulo 8 where possible (kBankGroups); a block of 8
-    // lanes then gathers 16-byte staged rows from distinct shared-memory bank groups.
+    // Sigma copies of the lists: the same entries per source, each list padded with zero entries
+    // to a multiple of kListPad and reordered so that the 8 entries one 128-bit shared-memory
+    // phase gathers have distinct targets modulo 8 where possible (kBankGroups).
+    int64_t *sig_s_ptr = nullptr, *sig_d_ptr = nullptr;  // [n+1], padded CSR offsets
+    int64_t sig_ns = 0, sig_nd = 0;
     uint32_t *s_pk_sig = nullptr;
     double *s_v64_sig = nullptr;
     int32_t *d_j_sig = nullptr;

@@ -815,18 +815,25 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
                 SBD_CUDA(cudaStreamSynchronize(w.s));
                 r.restarts++;
             }
-            // 2g. orthogonalise the corrections twice against V (classical Gram-Schmidt), normalise, append
+            // 2g. orthogonalise the corrections against V by classical Gram-Schmidt, with a second
+            // pass when the first removed more than 1/sqrt(2) of the norm (the DGKS criterion);
+            // normalise and append
             const int k_old = k;
             for (int j = 0; j < nroots; ++j) {
                 if (rn[j] <= tol) continue;
                 double *t = TC + j * ld;
                 w.dots(V, ld, k, t, coef, 1, nullptr, 0, dscr + 0);     // c = V^T t, |t|^2 before
-                w.axpys(V, ld, k, coef, t);                              // t -= V c
-                w.dots(V, ld, k, t, coef, 1);                           // c = V^T t
                 w.axpys(V, ld, k, coef, t, dscr + 1);                   // t -= V c, |t|^2 after
                 double nn[2];
                 SBD_CUDA(cudaMemcpyAsync(nn, dscr, sizeof(nn), cudaMemcpyDeviceToHost, w.s));
                 SBD_CUDA(cudaStreamSynchronize(w.s));
+                if (!(nn[1] > 0.5 * nn[0])) {
+                    w.dots(V, ld, k, t, coef, 1);                       // c = V^T t
+                    w.axpys(V, ld, k, coef, t, dscr + 1);               // t -= V c, |t|^2 after
+                    SBD_CUDA(cudaMemcpyAsync(nn + 1, dscr + 1, sizeof(double), cudaMemcpyDeviceToHost, w.s));
+                    SBD_CUDA(cudaStreamSynchronize(w.s));
+                    r.reorthogonalisations++;
+                }
                 const double n0 = sqrt(nn[0]), n1 = sqrt(nn[1]);
                 if (!(n1 > 1e-10 * n0) || !std::isfinite(n1)) continue;
                 w.scale(t, V + k * ld, 1.0 / n1);

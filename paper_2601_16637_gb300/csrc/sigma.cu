@@ -22,9 +22,10 @@
 // pass adds into it in program order, so results are deterministic.  Rows of
 // C are staged in shared memory, R rows interleaved per column so one vector
 // load fetches the same column of all R rows; the inner gathers then hit
-// shared memory only.  Excitation entries are read in batches of kBatch per
-// lane before any of them is used, and the next column's list bounds are
-// prefetched, so each lane keeps several L2 requests in flight.
+// shared memory only.  The lists are the padded sigma copies: each lane of an
+// 8-lane group fetches 4 entries with 16-byte loads, and the next column's
+// list bounds are prefetched.  The phase of a single is folded into the
+// shared-memory coefficient tables, which are indexed by 2*code + (phase<0).
 // Precision T = double (FP64) or float (mixed: FP32 amplitudes, integrals,
 // products and per-list sums, each list sum and the diagonal term accumulated
 // into the FP64 output).
@@ -36,7 +37,6 @@ namespace {
 
 constexpr int kGroup = 8;  // lanes cooperating on one output column
 constexpr int kGroupsPerWarp = 32 / kGroup;
-constexpr int kBatch = 4;  // entries each lane loads before using them
 
 template <typename T>
 struct Threads;
@@ -111,27 +111,32 @@ __device__ __forceinline__ T pick(const T (&v)[R], int i)
 __host__ __device__ constexpr size_t round16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 __device__ __forceinline__ int pk_j(uint32_t pk) { return (int)(pk & kPackJMask); }
-__device__ __forceinline__ int pk_code(uint32_t pk) { return (int)((pk >> kPackCodeShift) & kPackCodeMask); }
-__device__ __forceinline__ bool pk_neg(uint32_t pk) { return (pk & kPackNegBit) != 0u; }
+__device__ __forceinline__ int pk_key(uint32_t pk) { return (int)(pk >> kPackKeyShift); }  // 2*code + neg
+__device__ __forceinline__ int pk_code(uint32_t pk) { return (int)(pk >> (kPackKeyShift + 1)); }
+__device__ __forceinline__ bool pk_neg(uint32_t pk) { return ((pk >> kPackKeyShift) & 1u) != 0u; }
 
-// Excitation lists of the column spin, in the layout each precision reads.
+// Excitation lists of the column spin (padded sigma copies), in the layout each precision
+// reads.  Every list starts at a multiple of kListPad entries, so a lane fetches 4 entries with
+// 16-byte loads.
 template <typename T>
 struct Lists;
 template <>
 struct Lists<float> {
     const uint2 *s;  // (packed single, value bits)
     const uint2 *d;  // (target, value bits)
-    __device__ void single(int64_t e, uint32_t &pk, float &v) const
+    __device__ void singles4(int64_t e, uint32_t (&pk)[4], float (&v)[4]) const
     {
-        const uint2 x = __ldg(s + e);
-        pk = x.x;
-        v = __uint_as_float(x.y);
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(s + e));
+        const uint4 b = __ldg(reinterpret_cast<const uint4 *>(s + e + 2));
+        pk[0] = a.x, v[0] = __uint_as_float(a.y), pk[1] = a.z, v[1] = __uint_as_float(a.w);
+        pk[2] = b.x, v[2] = __uint_as_float(b.y), pk[3] = b.z, v[3] = __uint_as_float(b.w);
     }
-    __device__ void dbl(int64_t e, int &j, float &v) const
+    __device__ void doubles4(int64_t e, int (&j)[4], float (&v)[4]) const
     {
-        const uint2 x = __ldg(d + e);
-        j = (int)x.x;
-        v = __uint_as_float(x.y);
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(d + e));
+        const uint4 b = __ldg(reinterpret_cast<const uint4 *>(d + e + 2));
+        j[0] = (int)a.x, v[0] = __uint_as_float(a.y), j[1] = (int)a.z, v[1] = __uint_as_float(a.w);
+        j[2] = (int)b.x, v[2] = __uint_as_float(b.y), j[3] = (int)b.z, v[3] = __uint_as_float(b.w);
     }
 };
 template <>
@@ -140,15 +145,21 @@ struct Lists<double> {
     const double *sv;
     const int32_t *dj;
     const double *dv;
-    __device__ void single(int64_t e, uint32_t &pk, double &v) const
+    __device__ void singles4(int64_t e, uint32_t (&pk)[4], double (&v)[4]) const
     {
-        pk = __ldg(spk + e);
-        v = __ldg(sv + e);
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(spk + e));
+        const double2 b = __ldg(reinterpret_cast<const double2 *>(sv + e));
+        const double2 c = __ldg(reinterpret_cast<const double2 *>(sv + e + 2));
+        pk[0] = a.x, pk[1] = a.y, pk[2] = a.z, pk[3] = a.w;
+        v[0] = b.x, v[1] = b.y, v[2] = c.x, v[3] = c.y;
     }
-    __device__ void dbl(int64_t e, int &j, double &v) const
+    __device__ void doubles4(int64_t e, int (&j)[4], double (&v)[4]) const
     {
-        j = __ldg(dj + e);
-        v = __ldg(dv + e);
+        const int4 a = __ldg(reinterpret_cast<const int4 *>(dj + e));
+        const double2 b = __ldg(reinterpret_cast<const double2 *>(dv + e));
+        const double2 c = __ldg(reinterpret_cast<const double2 *>(dv + e + 2));
+        j[0] = a.x, j[1] = a.y, j[2] = a.z, j[3] = a.w;
+        v[0] = b.x, v[1] = b.y, v[2] = c.x, v[3] = c.y;
     }
 };
 
@@ -194,19 +205,22 @@ __global__ void __launch_bounds__(Threads<T>::value) row_pass_kernel(const RowAr
                 VecIO<T, R>::st(Xs + c * R, v);
             }
         }
-        for (int code = tid; code < n2; code += kThreads) {
+        // sign-folded J table: row key = 2*code + neg holds (neg ? -1 : 1) * J_r[code]; code 0 rows
+        // stay zero (no single has code 0; padding entries point there)
+        for (int key = tid; key < 2 * n2; key += kThreads) {
+            const int code = key >> 1;
             T v[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 double s = 0.0;
-                if (r < nr)
+                if (r < nr && code != 0)
                     for (uint64_t m = a.row_strings[r0 + r]; m; m &= m - 1ull) {
                         const int k = __ffsll((long long)m) - 1;
                         s += __ldg(a.eri + (size_t)code * n2 + (size_t)k * (a.norb + 1));
                     }
-                v[r] = (T)s;
+                v[r] = (T)((key & 1) ? -s : s);
             }
-            VecIO<T, R>::st(Js + (size_t)code * R, v);
+            VecIO<T, R>::st(Js + (size_t)key * R, v);
         }
         __syncthreads();
 
@@ -232,46 +246,32 @@ __global__ void __launch_bounds__(Threads<T>::value) row_pass_kernel(const RowAr
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[r] = T(0);
             if (valid) {
-                for (int64_t eb = s0 + lig; eb < s1; eb += kGroup * kBatch) {
-                    uint32_t pk[kBatch];
-                    T v[kBatch];
+                const int ls = (int)(s1 - s0), ld = (int)(d1 - d0);
+                for (int i = kListPad * lig; i < ls; i += kGroup * kListPad) {
+                    uint32_t pk[4];
+                    T v[4];
+                    a.lists.singles4(s0 + i, pk, v);
 #pragma unroll
-                    for (int u = 0; u < kBatch; ++u) {
-                        pk[u] = 0u;
-                        v[u] = T(0);
-                        if (eb + u * kGroup < s1) a.lists.single(eb + u * kGroup, pk[u], v[u]);
-                    }
+                    for (int u = 0; u < 4; ++u) {
+                        T xj[R], jv[R];
+                        if (STAGED) VecIO<T, R>::ld(Xs + (size_t)pk_j(pk[u]) * R, xj);
+                        else xj[0] = a.X[r0 * a.ncol + pk_j(pk[u])];
+                        VecIO<T, R>::ld(Js + (size_t)pk_key(pk[u]) * R, jv);
 #pragma unroll
-                    for (int u = 0; u < kBatch; ++u) {
-                        if (eb + u * kGroup < s1) {
-                            T xj[R], jv[R];
-                            if (STAGED) VecIO<T, R>::ld(Xs + (size_t)pk_j(pk[u]) * R, xj);
-                            else xj[0] = a.X[r0 * a.ncol + pk_j(pk[u])];
-                            VecIO<T, R>::ld(Js + (size_t)pk_code(pk[u]) * R, jv);
-                            const bool neg = pk_neg(pk[u]);
-#pragma unroll
-                            for (int r = 0; r < R; ++r) acc[r] += (neg ? v[u] - jv[r] : v[u] + jv[r]) * xj[r];
-                        }
+                        for (int r = 0; r < R; ++r) acc[r] += (v[u] + jv[r]) * xj[r];
                     }
                 }
-                for (int64_t eb = d0 + lig; eb < d1; eb += kGroup * kBatch) {
-                    int jj[kBatch];
-                    T v[kBatch];
+                for (int i = kListPad * lig; i < ld; i += kGroup * kListPad) {
+                    int jj[4];
+                    T v[4];
+                    a.lists.doubles4(d0 + i, jj, v);
 #pragma unroll
-                    for (int u = 0; u < kBatch; ++u) {
-                        jj[u] = 0;
-                        v[u] = T(0);
-                        if (eb + u * kGroup < d1) a.lists.dbl(eb + u * kGroup, jj[u], v[u]);
-                    }
+                    for (int u = 0; u < 4; ++u) {
+                        T xj[R];
+                        if (STAGED) VecIO<T, R>::ld(Xs + (size_t)jj[u] * R, xj);
+                        else xj[0] = a.X[r0 * a.ncol + jj[u]];
 #pragma unroll
-                    for (int u = 0; u < kBatch; ++u) {
-                        if (eb + u * kGroup < d1) {
-                            T xj[R];
-                            if (STAGED) VecIO<T, R>::ld(Xs + (size_t)jj[u] * R, xj);
-                            else xj[0] = a.X[r0 * a.ncol + jj[u]];
-#pragma unroll
-                            for (int r = 0; r < R; ++r) acc[r] += v[u] * xj[r];
-                        }
+                        for (int r = 0; r < R; ++r) acc[r] += v[u] * xj[r];
                     }
                 }
             }
@@ -350,11 +350,14 @@ __global__ void __launch_bounds__(Threads<T>::value) ab_pass_kernel(const AbArgs
                     VecIO<T, R>::st(Cs + c * R, v);
                 }
             }
-            for (int code = tid; code < n2; code += kThreads) {
+            // sign-folded W: row key = 2*rs + t holds (t ? -1 : 1) * u_k (p_k q_k|rs); rs = 0 rows zero
+            for (int key = tid; key < 2 * n2; key += kThreads) {
+                const int code = key >> 1;
+                const T sg = (key & 1) ? T(-1) : T(1);
                 T v[R];
 #pragma unroll
-                for (int k = 0; k < R; ++k) v[k] = u[k] * __ldg(a.eri + (size_t)pq[k] * n2 + code);
-                VecIO<T, R>::st(Ws + (size_t)code * R, v);
+                for (int k = 0; k < R; ++k) v[k] = code ? sg * u[k] * __ldg(a.eri + (size_t)pq[k] * n2 + code) : T(0);
+                VecIO<T, R>::st(Ws + (size_t)key * R, v);
             }
             __syncthreads();
 
@@ -374,26 +377,29 @@ __global__ void __launch_bounds__(Threads<T>::value) ab_pass_kernel(const AbArgs
                 }
                 T acc = T(0);
                 if (valid) {
-                    for (int64_t eb = b0 + lig; eb < b1; eb += kGroup * kBatch) {
-                        uint32_t pk[kBatch];
+                    const int lb = (int)(b1 - b0);
+                    for (int i = kListPad * lig; i < lb; i += kGroup * kListPad) {
+                        const uint4 p4 = __ldg(reinterpret_cast<const uint4 *>(a.bs_pk + b0 + i));
+                        const uint32_t pk[4] = {p4.x, p4.y, p4.z, p4.w};
+                        T part[4];
 #pragma unroll
-                        for (int t = 0; t < kBatch; ++t) {
-                            const int64_t e = eb + t * kGroup;
-                            pk[t] = e < b1 ? __ldg(a.bs_pk + e) : 0u;
-                        }
+                        for (int t = 0; t < 4; ++t) {
+                            T cv[R], wv[R];
+                            if (STAGED) VecIO<T, R>::ld(Cs + (size_t)pk_j(pk[t]) * R, cv);
+                            else cv[0] = a.C[ja[0] * a.nB + pk_j(pk[t])];
+                            VecIO<T, R>::ld(Ws + (size_t)pk_key(pk[t]) * R, wv);
+                            if constexpr (sizeof(T) == 4) {
+                                // FP32: one short chain per entry keeps the four entries independent
+                                part[t] = wv[0] * cv[0];
 #pragma unroll
-                        for (int t = 0; t < kBatch; ++t) {
-                            if (eb + t * kGroup < b1) {
-                                T cv[R], wv[R];
-                                if (STAGED) VecIO<T, R>::ld(Cs + (size_t)pk_j(pk[t]) * R, cv);
-                                else cv[0] = a.C[ja[0] * a.nB + pk_j(pk[t])];
-                                VecIO<T, R>::ld(Ws + (size_t)pk_code(pk[t]) * R, wv);
-                                T d = T(0);
+                                for (int k = 1; k < R; ++k) part[t] = fma(wv[k], cv[k], part[t]);
+                            } else {
+                                // FP64 is bound by the FP64 pipe: a single chain needs the fewest operations
 #pragma unroll
-                                for (int k = 0; k < R; ++k) d += wv[k] * cv[k];
-                                acc += pk_neg(pk[t]) ? -d : d;
+                                for (int k = 0; k < R; ++k) acc = fma(wv[k], cv[k], acc);
                             }
                         }
+                        if constexpr (sizeof(T) == 4) acc += (part[0] + part[1]) + (part[2] + part[3]);
                     }
                 }
 #pragma unroll
@@ -431,7 +437,7 @@ PassCfg choose(int64_t ncol, int n2, size_t elem, int rmax, size_t limit)
 {
     PassCfg p;
     for (int R = rmax; R >= 1; R /= 2) {
-        size_t b = round16((size_t)ncol * R * elem) + (size_t)n2 * R * elem;
+        size_t b = round16((size_t)ncol * R * elem) + (size_t)2 * n2 * R * elem;
         if (b <= limit) {
             p.R = R;
             p.staged = true;
@@ -441,7 +447,7 @@ PassCfg choose(int64_t ncol, int n2, size_t elem, int rmax, size_t limit)
     }
     p.R = 1;
     p.staged = false;
-    p.smem = (size_t)n2 * elem;
+    p.smem = (size_t)2 * n2 * elem;
     return p;
 }
 
@@ -550,8 +556,8 @@ void apply(Ctx &c, const T *C, double *S, const double *c64, cudaStream_t s)
     rb.row_strings = ta.strings;
     rb.norb = c.norb;
     rb.eri = c.eri64;
-    rb.s_ptr = tb.s_ptr;
-    rb.d_ptr = tb.d_ptr;
+    rb.s_ptr = tb.sig_s_ptr;
+    rb.d_ptr = tb.sig_d_ptr;
     rb.lists = lists_of<T>(tb);
     timed(c, base + 1, s, [&] { launch_row<T>(rb, choose(c.nB, n2, sizeof(T), rmax, lim), s); });
 
@@ -565,8 +571,8 @@ void apply(Ctx &c, const T *C, double *S, const double *c64, cudaStream_t s)
     ra.hd = nullptr;
     ra.xd64 = nullptr;
     ra.row_strings = tb.strings;
-    ra.s_ptr = ta.s_ptr;
-    ra.d_ptr = ta.d_ptr;
+    ra.s_ptr = ta.sig_s_ptr;
+    ra.d_ptr = ta.sig_d_ptr;
     ra.lists = lists_of<T>(ta);
     timed(c, base + 2, s, [&] { launch_row<T>(ra, choose(c.nA, n2, sizeof(T), rmax, lim), s); });
 
@@ -577,9 +583,9 @@ void apply(Ctx &c, const T *C, double *S, const double *c64, cudaStream_t s)
     ab.nB = c.nB;
     ab.norb = c.norb;
     ab.eri = sizeof(T) == 4 ? (const T *)(const void *)c.eri32 : (const T *)(const void *)c.eri64;
-    ab.as_ptr = ta.s_ptr;
-    ab.as_pk = ta.s_pk_sig;
-    ab.bs_ptr = tb.s_ptr;
+    ab.as_ptr = ta.s_ptr;      // canonical alpha lists: exact counts for the row groups
+    ab.as_pk = ta.s_pk;
+    ab.bs_ptr = tb.sig_s_ptr;  // padded beta lists for 16-byte loads
     ab.bs_pk = tb.s_pk_sig;
     timed(c, base + 3, s, [&] { launch_ab<T>(ab, choose(c.nB, n2, sizeof(T), rmax, lim), s); });
 }

@@ -118,9 +118,8 @@ __device__ __forceinline__ void store_single(const TableOut &o, int64_t pos, con
     o.s_orb[4 * pos + 3] = e.orb[3];
     o.s_sign[pos] = e.sign;
     o.s_v[pos] = e.val;
-    uint32_t pk = (uint32_t)e.j | ((uint32_t)(e.orb[0] * norb + e.orb[2]) << kPackCodeShift);
-    if (e.sign < 0) pk |= kPackNegBit;
-    o.s_pk[pos] = pk;
+    const uint32_t key = 2u * (uint32_t)(e.orb[0] * norb + e.orb[2]) + (e.sign < 0 ? 1u : 0u);
+    o.s_pk[pos] = (uint32_t)e.j | (key << kPackKeyShift);
 }
 
 __device__ __forceinline__ void store_double(const TableOut &o, int64_t pos, const Entry &e)
@@ -352,27 +351,36 @@ __global__ void ediag_kernel(const uint64_t *S, int64_t n, int norb, const doubl
     }
 }
 
-// Bank-aware order of each source's list: entry e with target residue r = j mod 8
-// and rank t among the entries of residue r goes to position
-//   sum_r' min(count[r'], t) + #{r' < r : count[r'] > t},
-// i.e. the list is read as rounds "rank 0 of every residue, rank 1 of every
-// residue, ..."; each aligned block of 8 then holds distinct residues except
-// where the residue counts are unequal.  One thread per source.
-__global__ void bank_order_kernel(const int64_t *__restrict__ ptr, int64_t n, const int32_t *__restrict__ j_src,
-                                  int64_t *perm)
+// Sigma order of each source's list.  The list is padded with empty slots to a multiple of
+// kListPad and laid out for 16-byte loads: lane l of an 8-lane group fetches slots 4l..4l+3 of
+// each 32-slot chunk, and one 128-bit shared-memory phase gathers slot 4l+u of every lane.
+// Entries are first ranked as rounds "rank 0 of every target residue mod 8, rank 1 of every
+// residue, ...", so that consecutive entries in that order have distinct residues where the
+// residue counts allow; each phase then receives a run of consecutive positions.
+// perm[sig_ptr[i] + slot] = index of the canonical entry, or -1 for padding.  One thread per source.
+__global__ void sigma_order_kernel(const int64_t *__restrict__ ptr, const int64_t *__restrict__ sig_ptr, int64_t n,
+                                   const int32_t *__restrict__ j_src, int64_t *perm)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = ptr[i], e = ptr[i + 1];
+        const int64_t b = ptr[i], e = ptr[i + 1], sb = sig_ptr[i], se = sig_ptr[i + 1];
+        const int L = (int)(e - b), Lp = (int)(se - sb);
+        for (int q = 0; q < Lp; ++q) perm[sb + q] = -1;  // slots no entry lands on stay padding
         int count[kBankGroups] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int64_t x = b; x < e; ++x) ++count[j_src[x] & (kBankGroups - 1)];
         int seen[kBankGroups] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int64_t x = b; x < e; ++x) {
             const int r = j_src[x] & (kBankGroups - 1);
             const int t = seen[r]++;
-            int64_t pos = 0;
+            int q = 0;  // position in round order
 #pragma unroll
-            for (int q = 0; q < kBankGroups; ++q) pos += min(count[q], t) + ((q < r && count[q] > t) ? 1 : 0);
-            perm[b + pos] = x;  // entry x goes to position b + pos
+            for (int w = 0; w < kBankGroups; ++w) q += min(count[w], t) + ((w < r && count[w] > t) ? 1 : 0);
+            // round-order position q -> slot: in a chunk of Lc slots (32, or what is left of a
+            // short list) m = Lc/4 lanes each fetch 4 slots, and phase u gathers slot 4*l + u of
+            // every lane l; position m*u + l goes to slot 4*l + u, so each phase reads m
+            // consecutive round-order positions
+            const int chunk = q / 32, within = q % 32;
+            const int m = min(32, Lp - chunk * 32) / 4;
+            perm[sb + chunk * 32 + 4 * (within % m) + within / m] = x;
         }
     }
 }
@@ -380,8 +388,19 @@ __global__ void bank_order_kernel(const int64_t *__restrict__ ptr, int64_t n, co
 template <typename V>
 __global__ void gather_kernel(const V *__restrict__ src, const int64_t *__restrict__ perm, V *dst, int64_t n)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = src[perm[i]];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = perm[i];
+        dst[i] = p >= 0 ? src[p] : V(0);
+    }
+}
+
+// padded counts: cnt[i] = ceil((ptr[i+1]-ptr[i]) / kListPad) * kListPad
+__global__ void padded_count_kernel(const int64_t *__restrict__ ptr, int64_t n, int64_t *cnt)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t L = ptr[i + 1] - ptr[i];
+        cnt[i] = (L + kListPad - 1) / kListPad * kListPad;
+    }
 }
 
 // (key, FP32 value) pairs for single 8-byte loads in the mixed sigma
@@ -491,12 +510,10 @@ void build_tables(Ctx &c, int spin)
     t.s_sign = dalloc_n<int8_t>(c, t.ns);
     t.s_pk = dalloc_n<uint32_t>(c, t.ns);
     t.s_v64 = dalloc_n<double>(c, t.ns);
-    t.s_pkv32 = dalloc_n<uint2>(c, t.ns);
     t.d_j = dalloc_n<int32_t>(c, t.nd);
     t.d_orb = dalloc_n<uint8_t>(c, 4 * t.nd);
     t.d_sign = dalloc_n<int8_t>(c, t.nd);
     t.d_v64 = dalloc_n<double>(c, t.nd);
-    t.d_jv32 = dalloc_n<uint2>(c, t.nd);
     o.s_ptr = t.s_ptr;
     o.d_ptr = t.d_ptr;
     o.s_j = t.s_j;
@@ -517,32 +534,45 @@ void build_tables(Ctx &c, int spin)
                                                                   c.h64, c.eri64, o);
         SBD_LAUNCH("enum_kernel(fill)");
     }
-    // sigma copies in bank-aware order
-    t.s_pk_sig = dalloc_n<uint32_t>(c, t.ns);
-    t.s_v64_sig = dalloc_n<double>(c, t.ns);
-    t.d_j_sig = dalloc_n<int32_t>(c, t.nd);
-    t.d_v64_sig = dalloc_n<double>(c, t.nd);
-    int64_t *perm = dalloc_n<int64_t>(c, (size_t)std::max(t.ns, t.nd));
+    // sigma copies: padded, bank-aware order
+    t.sig_s_ptr = dalloc_n<int64_t>(c, n + 1);
+    t.sig_d_ptr = dalloc_n<int64_t>(c, n + 1);
+    padded_count_kernel<<<blocks_for(n, 256), 256, 0, c.stream>>>(t.s_ptr, n, cnt);
+    padded_count_kernel<<<blocks_for(n, 256), 256, 0, c.stream>>>(t.d_ptr, n, cnt + n);
+    SBD_LAUNCH("padded_count_kernel");
+    scan_kernel<<<1, 1024, 0, c.stream>>>(cnt, n, t.sig_s_ptr);
+    scan_kernel<<<1, 1024, 0, c.stream>>>(cnt + n, n, t.sig_d_ptr);
+    SBD_LAUNCH("scan_kernel(sigma lists)");
+    SBD_CUDA(cudaMemcpyAsync(&t.sig_ns, t.sig_s_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, c.stream));
+    SBD_CUDA(cudaMemcpyAsync(&t.sig_nd, t.sig_d_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, c.stream));
+    SBD_CUDA(cudaStreamSynchronize(c.stream));
+    t.s_pk_sig = dalloc_n<uint32_t>(c, t.sig_ns);
+    t.s_v64_sig = dalloc_n<double>(c, t.sig_ns);
+    t.s_pkv32 = dalloc_n<uint2>(c, t.sig_ns);
+    t.d_j_sig = dalloc_n<int32_t>(c, t.sig_nd);
+    t.d_v64_sig = dalloc_n<double>(c, t.sig_nd);
+    t.d_jv32 = dalloc_n<uint2>(c, t.sig_nd);
+    int64_t *perm = dalloc_n<int64_t>(c, (size_t)std::max<int64_t>(std::max(t.sig_ns, t.sig_nd), 1));
     const int ob = blocks_for(n, 128);
-    if (t.ns) {
-        bank_order_kernel<<<ob, 128, 0, c.stream>>>(t.s_ptr, n, t.s_j, perm);
-        SBD_LAUNCH("bank_order_kernel(singles)");
-        const int gb = blocks_for(t.ns, 256, 16384);
-        gather_kernel<uint32_t><<<gb, 256, 0, c.stream>>>(t.s_pk, perm, t.s_pk_sig, t.ns);
-        gather_kernel<double><<<gb, 256, 0, c.stream>>>(t.s_v64, perm, t.s_v64_sig, t.ns);
+    if (t.sig_ns) {
+        sigma_order_kernel<<<ob, 128, 0, c.stream>>>(t.s_ptr, t.sig_s_ptr, n, t.s_j, perm);
+        SBD_LAUNCH("sigma_order_kernel(singles)");
+        const int gb = blocks_for(t.sig_ns, 256, 16384);
+        gather_kernel<uint32_t><<<gb, 256, 0, c.stream>>>(t.s_pk, perm, t.s_pk_sig, t.sig_ns);
+        gather_kernel<double><<<gb, 256, 0, c.stream>>>(t.s_v64, perm, t.s_v64_sig, t.sig_ns);
         SBD_LAUNCH("gather_kernel(singles)");
-        pair_kernel<<<gb, 256, 0, c.stream>>>(t.s_pk_sig, t.s_v64_sig, t.s_pkv32, t.ns);
+        pair_kernel<<<gb, 256, 0, c.stream>>>(t.s_pk_sig, t.s_v64_sig, t.s_pkv32, t.sig_ns);
         SBD_LAUNCH("pair_kernel(singles)");
     }
-    if (t.nd) {
-        bank_order_kernel<<<ob, 128, 0, c.stream>>>(t.d_ptr, n, t.d_j, perm);
-        SBD_LAUNCH("bank_order_kernel(doubles)");
-        const int gb = blocks_for(t.nd, 256, 16384);
-        gather_kernel<int32_t><<<gb, 256, 0, c.stream>>>(t.d_j, perm, t.d_j_sig, t.nd);
-        gather_kernel<double><<<gb, 256, 0, c.stream>>>(t.d_v64, perm, t.d_v64_sig, t.nd);
+    if (t.sig_nd) {
+        sigma_order_kernel<<<ob, 128, 0, c.stream>>>(t.d_ptr, t.sig_d_ptr, n, t.d_j, perm);
+        SBD_LAUNCH("sigma_order_kernel(doubles)");
+        const int gb = blocks_for(t.sig_nd, 256, 16384);
+        gather_kernel<int32_t><<<gb, 256, 0, c.stream>>>(t.d_j, perm, t.d_j_sig, t.sig_nd);
+        gather_kernel<double><<<gb, 256, 0, c.stream>>>(t.d_v64, perm, t.d_v64_sig, t.sig_nd);
         SBD_LAUNCH("gather_kernel(doubles)");
         pair_kernel<<<gb, 256, 0, c.stream>>>(reinterpret_cast<const uint32_t *>(t.d_j_sig), t.d_v64_sig, t.d_jv32,
-                                               t.nd);
+                                               t.sig_nd);
         SBD_LAUNCH("pair_kernel(doubles)");
     }
     dfree(c, perm);

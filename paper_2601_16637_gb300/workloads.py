@@ -168,6 +168,7 @@ def make(name: str, norb: int, nalpha: int, nbeta: int, nA: int | None, nB: int 
 #   cfg2: norb=16, 5+5, |A|=|B|=2,000 (4.0e6 determinants), lam 0.35, 3 roots, tol 1e-8
 #   cfg3: norb=29, 10+10, |A|=|B|=10,000 (1.0e8 determinants), lam 0.25, mixed precision,
 #         1 root, subspace <= 24
+#   cfg3-6000: cfg3 with |A|=|B|=6,000 (3.6e7 determinants)
 CONFIGS = {
     "cfg1": dict(norb=8, nalpha=4, nbeta=4, nA=None, nB=None, lam=0.0, seed=0,
                  nroots=1, tol=1e-10, precision="fp64"),
@@ -175,6 +176,10 @@ CONFIGS = {
                  nroots=3, tol=1e-8, precision="fp64"),
     "cfg3": dict(norb=29, nalpha=10, nbeta=10, nA=10000, nB=10000, lam=0.25, seed=2,
                  nroots=1, tol=1e-6, precision="mixed", max_subspace=24),
+    # the norb=29 workload at |A|=|B|=6,000 (3.6e7 determinants, the paper's determinant count):
+    # same kernels and launch shapes, a smaller footprint for profiler captures
+    "cfg3-6000": dict(norb=29, nalpha=10, nbeta=10, nA=6000, nB=6000, lam=0.25, seed=2,
+                      nroots=1, tol=1e-6, precision="mixed", max_subspace=24),
 }
 
 
