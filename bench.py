@@ -342,6 +342,13 @@ def main():
         achieved = flops[dominant] / (ms_dom * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    if roof["bound"] == "alu":
+        # the sigma passes gather both FMA operands from shared memory: one 128-byte wavefront per SM
+        # clock feeds 128 / (2 * elem) multiply-adds, the ceiling of this design below the ALU peak
+        ceil_tf = NUM_SMS * (128 // (2 * elem)) * 2 * sm_max * 1e6 / 1e12
+        roof["smem_ceiling"] = {"peak": ceil_tf, "unit": "TFLOP/s", "frac": roof["achieved"] / ceil_tf,
+                                "basis": f"one 128-byte shared-memory wavefront per SM clock = "
+                                         f"{128 // (2 * elem)} FMA with two {elem}-byte operands"}
     roof["kernel"] = f"{dominant} ({p_main})"
     roof["peak_source"] = (f"{peak_src} HBM copy" if roof["bound"] == "hbm" else
                            ("FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x max SM clock" if p_main == "mixed"
