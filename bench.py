@@ -218,6 +218,172 @@ def traffic_record(kernel: str):
     return None
 
 
+# ---------------------------------------------------------------------------
+# batched and served solves (the engine)
+
+
+def serial_fp64(B, wl, stream):
+    """The plain per-instance path: sbd_create + FP64 sbd_davidson + sbd_destroy, same stopping rule."""
+    import torch
+
+    t0 = time.perf_counter()
+    with B.SBD.from_workload(wl, tol_energy=wl.extra.get("tol_energy", 0.0), stream=stream) as g:
+        s = g.davidson(1, wl.tol, "fp64", vectors=None)
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, float(s.energies[0]), int(s.status), s.report
+
+
+def engine_line(args, metric_value, elapsed, n_jobs, stats, extra, clk, config):
+    return {"metric": METRIC, "value": metric_value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config,
+            "solves_per_s": n_jobs / elapsed, "gpu_launches": int(stats["kernel_launches"]),
+            "graph_launches": int(stats["graph_launches"]), "engine": stats, "clocks": clk, **extra}
+
+
+def run_batch(args):
+    """64 independent instances in one engine (persistent launches, CUDA graphs), against the
+    serial FP64 per-instance path on the same instances and stopping rule."""
+    import torch
+
+    from paper_2601_16637_gb300 import binding as B
+    from paper_2601_16637_gb300 import workloads as W
+
+    B.load(build_if_missing=True)
+    insts = W.batch_instances(args.batch_n)
+    opts = dict(max_slots=len(insts), max_subspace=12, max_norb=26, max_strings=5000)
+    small = sorted(insts, key=lambda w: w.ndets)[:2]
+    for _ in range(args.warmup):
+        with B.Engine(**opts) as e:
+            for w in small:
+                e.submit(w, tol=w.tol, tol_energy=w.extra["tol_energy"])
+            e.run()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    elapsed, dets_sigma, results, stats = 0.0, 0.0, [], None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        with B.Engine(**opts) as e:
+            ids = [e.submit(w, tol=w.tol, tol_energy=w.extra["tol_energy"]) for w in insts]
+            e.run()
+            torch.cuda.synchronize()
+            elapsed += time.perf_counter() - t0
+            results = [e.result(j) for j in ids]
+            stats = e.stats()
+        dets_sigma += sum(r["ndets"] * (r["sigma_mixed"] + r["sigma_fp64"]) for r in results)
+    clk = clocks.stop()
+    stream = torch.cuda.current_stream()
+    serial_t, dE, serial_status = 0.0, 0.0, []
+    for w, r in zip(insts, results):
+        t, e64, st, _ = serial_fp64(B, w, stream)
+        serial_t += t
+        serial_status.append(st)
+        dE = max(dE, abs(e64 - r["energy"]))
+    per_run = elapsed / args.steps
+    extra = {"batch": {"instances": len(insts), "total_dets": int(sum(w.ndets for w in insts)),
+                       "status_counts": {str(k): sum(1 for r in results if r["status"] == k)
+                                         for k in sorted({r["status"] for r in results})},
+                       "iterations_mean": float(np.mean([r["iterations"] for r in results])),
+                       "seconds_per_batch": per_run},
+             "vs_serial_fp64": {"seconds": serial_t, "solves_per_s": len(insts) / serial_t,
+                                "speedup": serial_t / per_run, "max_abs_dE_Ha": dE,
+                                "statuses": {str(k): serial_status.count(k) for k in sorted(set(serial_status))}}}
+    config = {"workload": f"batch{len(insts)}: {len(insts)} instances, norb in {{16,20,24,26}}, "
+                          f"nalpha=nbeta=round(norb/3), |A|,|B| uniform in [500,5000], own integrals each; "
+                          f"1 root, mixed sigma, residual <= 1e-3 and Ritz-value change <= 1e-6 Ha",
+              "step": "one engine run over all instances (admission, tables, Davidson, FP64 check)",
+              "max_subspace": 12, "rows_per_item": stats["rows_per_item"],
+              "l2": "inputs larger than L2 (vectors of all instances ~4 GB)"}
+    print(json.dumps(engine_line(args, dets_sigma / elapsed, elapsed, len(insts) * args.steps, stats, extra, clk,
+                                 config)), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """A finite Poisson stream of jobs served by one engine (continuous batching under a memory
+    budget), against a FIFO queue served one job at a time by the serial FP64 path."""
+    import torch
+
+    from paper_2601_16637_gb300 import binding as B
+    from paper_2601_16637_gb300 import workloads as W
+
+    B.load(build_if_missing=True)
+    trace = W.serving_trace(n=args.requests, rate=args.rate, max_strings=args.max_strings)
+    t_build = time.perf_counter()
+    jobs = [(t, W.make_job(spec, te)) for t, spec, te in trace]
+    t_build = time.perf_counter() - t_build
+    max_norb = max(w.norb for _, w in jobs)
+    opts = dict(max_slots=64, max_subspace=12, max_norb=max_norb, max_strings=args.max_strings,
+                hbm_budget_bytes=int(args.budget_gb * 1e9))
+    small = sorted((w for _, w in jobs), key=lambda w: w.ndets)[:2]
+    for _ in range(args.warmup):
+        with B.Engine(**opts) as e:
+            for w in small:
+                e.submit(w, tol=w.tol, tol_energy=w.extra["tol_energy"])
+            e.run()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    with B.Engine(**opts) as e:
+        base = e.clock()
+        ids, i, n = [], 0, len(jobs)
+        remaining = 0
+        while i < n or remaining > 0:
+            now = e.clock() - base
+            while i < n and jobs[i][0] <= now:
+                w = jobs[i][1]
+                ids.append(e.submit(w, tol=w.tol, tol_energy=w.extra["tol_energy"]))
+                i += 1
+            if e.stats()["active"] + e.stats()["pending"] > 0:
+                remaining = e.step()
+            else:
+                remaining = 0
+                if i < n:
+                    time.sleep(max(0.0, min(0.01, jobs[i][0] - (e.clock() - base))))
+        results = [e.result(j) for j in ids]
+        stats = e.stats()
+    clk = clocks.stop()
+    arrivals = np.array([t for t, _ in jobs])
+    done = np.array([r["t_done"] - base for r in results])
+    lat = done - arrivals
+    span = float(done.max() - arrivals.min())
+    dets_sigma = sum(r["ndets"] * (r["sigma_mixed"] + r["sigma_fp64"]) for r in results)
+    # serial FP64 per-instance path: measured service time per job, FIFO queue on the same arrivals
+    stream = torch.cuda.current_stream()
+    service, dE, st64 = [], 0.0, []
+    for (t, w), r in zip(jobs, results):
+        ts, e64, st, _ = serial_fp64(B, w, stream)
+        service.append(ts)
+        st64.append(st)
+        dE = max(dE, abs(e64 - r["energy"]))
+    fin, tcur = [], 0.0
+    for a, sv in zip(arrivals, service):
+        tcur = max(tcur, a) + sv
+        fin.append(tcur)
+    lat64 = np.array(fin) - arrivals
+    span64 = float(fin[-1] - arrivals.min())
+    extra = {"serving": {"requests": n, "rate_per_s": args.rate, "p50_s": float(np.percentile(lat, 50)),
+                         "p99_s": float(np.percentile(lat, 99)), "makespan_s": span,
+                         "status_counts": {str(k): sum(1 for r in results if r["status"] == k)
+                                           for k in sorted({r["status"] for r in results})},
+                         "max_active": None, "bytes_peak": stats["bytes_peak"], "budget_bytes": opts["hbm_budget_bytes"],
+                         "job_build_s": t_build},
+             "vs_serial_fp64": {"p50_s": float(np.percentile(lat64, 50)), "p99_s": float(np.percentile(lat64, 99)),
+                                "makespan_s": span64, "solves_per_s": n / span64,
+                                "service_s_total": float(sum(service)), "max_abs_dE_Ha": dE,
+                                "statuses": {str(k): st64.count(k) for k in sorted(set(st64))}}}
+    config = {"workload": f"serve: {n} Poisson arrivals at {args.rate:g}/s, norb in {{24,32,40,48,58}}, "
+                          f"nalpha=nbeta=round(norb/3), |A|=|B| log-uniform in [300,{args.max_strings}], own "
+                          f"integrals each; 1 root, mixed sigma, residual <= 1e-3 and Ritz-value change <= 1e-6 Ha; "
+                          f"admission budget {args.budget_gb:g} GB",
+              "step": "the whole trace (arrival of the first job to completion of the last)",
+              "l2": "inputs larger than L2"}
+    args.steps = 1
+    print(json.dumps(engine_line(args, dets_sigma / span, span, n, stats, extra, clk, config)), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -229,11 +395,20 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-n", type=int, default=64, help="instances of the batch64 workload")
+    ap.add_argument("--requests", type=int, default=40, help="jobs of the serve workload")
+    ap.add_argument("--rate", type=float, default=20.0, help="arrivals per second of the serve workload")
+    ap.add_argument("--max-strings", type=int, default=5000, help="largest |A| = |B| of the serve workload")
+    ap.add_argument("--budget-gb", type=float, default=160.0, help="engine admission budget of the serve workload")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     import torch
 

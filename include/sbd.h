@@ -62,6 +62,7 @@ enum {
     SBD_ERR_NONFINITE = -8,       /* NaN or Inf in h or eri */
     SBD_ERR_BREAKDOWN = -9,       /* Davidson could not extend its subspace */
     SBD_ERR_UNSUPPORTED = -10,    /* a size this build does not handle */
+    SBD_PENDING = 2,              /* engine job not finished yet (sbd_engine_result) */
 };
 
 /* Device allocator hooks.  alloc returns a device pointer (16-byte aligned
@@ -81,6 +82,8 @@ typedef struct {
     sbd_free_fn free;
     void *alloc_ctx;
     int timing;              /* nonzero: time every sigma kernel with CUDA events (sbd_kernel_times) */
+    double tol_energy;       /* > 0: a root also needs |theta_k - theta_(k-1)| <= tol_energy between
+                                consecutive iterations to count as converged (default 0: off) */
 } sbd_options;
 
 typedef struct {
@@ -239,6 +242,118 @@ int64_t sbd_launch_count(void);
 #define SBD_NOALLOC_MAX_STRINGS 65536
 int sbd_sort_strings_noalloc(const uint64_t *keys_dev, int64_t n, int norb, int nel, uint64_t *sorted_dev,
                              int64_t *bad_index_host, void *stream);
+
+/*
+ * sbd_sigma_batched -- sigma = H c of n instances in one batched launch
+ * sequence: a transpose and the beta, alpha and alpha-beta passes each run as
+ * one persistent launch whose CTAs take (instance, row-group) work items from
+ * a device counter (the batched engine's sigma; paper Sec. II-A/B Eq. 4).
+ *   handles      n handles on the same device (distinct)
+ *   c_dev[i]     device pointer, handle i's [nA][nB] vector (float for
+ *                SBD_MIXED, double for SBD_FP64), sorted-string order
+ *   sigma_dev[i] device pointer, [nA][nB] doubles, written
+ *   rows_per_item rows of C staged per work item: 1, 2 or (mixed) 4; 0 picks
+ *                the largest that fits shared memory for every instance
+ * Each output element is computed by the same arithmetic as sbd_sigma with
+ * the same rows per item.  Enqueued on `stream` (the handles' work buffers are
+ * used), then synchronised.
+ */
+int sbd_sigma_batched(int n, const sbd_handle *handles, const void *const *c_dev, double *const *sigma_dev,
+                      sbd_precision prec, int rows_per_item, void *stream);
+
+/*
+ * Batched and served solves.  No counterpart in the paper: an engine runs the
+ * Davidson iterations (Sec. II-C, the Eq. 7 preconditioner) of many
+ * independent instances ("jobs") together on one device.  Per engine
+ * iteration, one set of persistent kernel launches covers every admitted job
+ * (the sigma work items and vector chunks of all jobs share each launch), and
+ * the iteration's launch sequence is captured once as two CUDA graphs that
+ * are replayed.  Jobs are admitted in submission order while a slot is free
+ * and their device memory fits the budget, iterate until converged, and leave,
+ * so jobs submitted while others run join them (continuous batching).  A job's
+ * arithmetic does not depend on the other jobs: its results are bitwise the
+ * same alone and in any mix.
+ *
+ * Per job: 1 root; sigma in mixed precision (SBD_MIXED) for the iterations;
+ * convergence when the mixed residual is <= tol and (tol_energy > 0) the
+ * change of the Ritz value since the previous iteration is <= tol_energy; the
+ * result is then checked with one FP64 sigma of the Ritz vector, whose FP64
+ * residual must also be <= tol (else the job iterates on with a halved mixed
+ * threshold).  Reported energy = FP64 Rayleigh quotient + ecore.
+ * Orthogonalisation: classical Gram-Schmidt, always two passes; thick restart
+ * to nkeep = max(2, max_subspace/3) Ritz vectors.
+ */
+typedef struct sbd_engine_s *sbd_engine;
+
+typedef struct {
+    int max_slots;           /* jobs on the device at once (default 64, at most 1024) */
+    int max_subspace;        /* Davidson basis vectors per job (default 12, 3..32) */
+    int max_iter;            /* iterations per job (default 200) */
+    int max_norb;            /* largest norb of a job (default 64) */
+    int max_strings;         /* largest |A| or |B| of a job (default 20000) */
+    int rows_per_item;       /* mixed sigma rows per work item: 1, 2, 4; 0 = autotune at the first step */
+    double delta;            /* preconditioner floor (default 1e-4) */
+    size_t hbm_budget_bytes; /* admission budget for the jobs' device memory; 0 = unlimited */
+    sbd_alloc_fn alloc;      /* NULL: cudaMallocAsync / cudaFreeAsync */
+    sbd_free_fn free;
+    void *alloc_ctx;
+} sbd_engine_options;
+
+typedef struct {
+    int status;          /* SBD_OK, SBD_NOT_CONVERGED, or an error (< 0) */
+    int iterations;      /* engine iterations the job took part in */
+    int sigma_mixed;     /* mixed sigma products */
+    int sigma_fp64;      /* FP64 sigma products (checks) */
+    int restarts;
+    double energy;       /* FP64 Rayleigh quotient of the returned vector, + ecore */
+    double residual;     /* its FP64 residual norm */
+    double energy_mixed; /* last mixed Ritz value, + ecore */
+    double t_submit;     /* engine clock (seconds since sbd_engine_create) */
+    double t_admit;
+    double t_done;
+    int64_t ndets;       /* nA * nB */
+} sbd_job_result;
+
+typedef struct {
+    int64_t steps;            /* sbd_engine_step calls that did work */
+    int64_t graph_launches;   /* CUDA graph replays */
+    int64_t kernel_launches;  /* kernels run by this engine (graph nodes included) */
+    int rows_per_item;        /* mixed sigma rows per work item in use */
+    double tune_ms[3];        /* autotuner: batched mixed sigma time with 4, 2, 1 rows (0 = not tried) */
+    size_t bytes_in_use;      /* device bytes held for admitted jobs */
+    size_t bytes_peak;
+    int active, pending, done;
+} sbd_engine_stats;
+
+void sbd_engine_default_options(sbd_engine_options *opt);
+/* One engine per device and stream; the stream is used for all its work. */
+int sbd_engine_create(sbd_engine *out, const sbd_engine_options *opt, void *stream);
+/* Frees every job's device memory; unfinished jobs are dropped. */
+int sbd_engine_destroy(sbd_engine engine);
+/*
+ * Queues a job (inputs as in sbd_create; host or device pointers, copied
+ * before return).  keep_vector != 0 keeps the eigenvector for
+ * sbd_engine_vector.  *job receives the job id.  Invalid inputs are reported
+ * here; errors found while the job runs are reported in its result.
+ */
+int sbd_engine_submit(sbd_engine engine, int norb, int nalpha, int nbeta, const double *h, const double *eri,
+                      const uint64_t *A, int64_t nA, const uint64_t *B, int64_t nB, double ecore, double tol,
+                      double tol_energy, int keep_vector, int64_t *job);
+/* One engine iteration: admit, iterate every admitted job once, retire the
+ * finished ones.  *remaining (may be NULL) = jobs pending or active after it. */
+int sbd_engine_step(sbd_engine engine, int *remaining);
+/* Steps until no job is pending or active. */
+int sbd_engine_run(sbd_engine engine);
+/* SBD_PENDING while the job runs; otherwise fills *out and returns SBD_OK. */
+int sbd_engine_result(sbd_engine engine, int64_t job, sbd_job_result *out);
+/* Copies a finished job's eigenvector (nA*nB doubles, sorted-string order;
+ * largest-magnitude component positive) to a host or device pointer. */
+int sbd_engine_vector(sbd_engine engine, int64_t job, double *out, int64_t n);
+/* Forgets a finished job (its result and vector). */
+int sbd_engine_release(sbd_engine engine, int64_t job);
+int sbd_engine_get_stats(sbd_engine engine, sbd_engine_stats *out);
+/* Seconds since sbd_engine_create on the engine's clock. */
+double sbd_engine_clock(sbd_engine engine);
 
 /* Message for the last failure on `handle` (NULL: on this thread); valid
  * until the next call on the same handle / thread. */

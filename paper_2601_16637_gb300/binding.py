@@ -38,7 +38,7 @@ class sbd_options(C.Structure):
     _fields_ = [("delta", C.c_double), ("max_subspace", C.c_int), ("max_iter", C.c_int),
                 ("hbm_budget_bytes", C.c_size_t), ("ecore", C.c_double), ("table_algo", C.c_int),
                 ("verbose", C.c_int), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("timing", C.c_int)]
+                ("timing", C.c_int), ("tol_energy", C.c_double)]
 
 
 class sbd_report(C.Structure):
@@ -49,6 +49,34 @@ class sbd_report(C.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class sbd_engine_options(C.Structure):
+    _fields_ = [("max_slots", C.c_int), ("max_subspace", C.c_int), ("max_iter", C.c_int),
+                ("max_norb", C.c_int), ("max_strings", C.c_int), ("rows_per_item", C.c_int),
+                ("delta", C.c_double), ("hbm_budget_bytes", C.c_size_t), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", C.c_void_p)]
+
+
+class sbd_job_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("sigma_mixed", C.c_int), ("sigma_fp64", C.c_int),
+                ("restarts", C.c_int), ("energy", C.c_double), ("residual", C.c_double),
+                ("energy_mixed", C.c_double), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double), ("ndets", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class sbd_engine_stats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("graph_launches", C.c_int64), ("kernel_launches", C.c_int64),
+                ("rows_per_item", C.c_int), ("tune_ms", C.c_double * 3), ("bytes_in_use", C.c_size_t),
+                ("bytes_peak", C.c_size_t), ("active", C.c_int), ("pending", C.c_int), ("done", C.c_int)]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["tune_ms"] = list(self.tune_ms)
+        return d
 
 
 class SbdError(RuntimeError):
@@ -82,7 +110,22 @@ _SIGNATURES = {
     "sbd_kernel_times": (_int, [_vp, _vp, _vp, _int]),
     "sbd_launch_count": (_i64, []),
     "sbd_sort_strings_noalloc": (_int, [_vp, _i64, _int, _int, _vp, C.POINTER(_i64), _vp]),
+    "sbd_sigma_batched": (_int, [_int, _vp, _vp, _vp, _int, _int, _vp]),
+    "sbd_engine_default_options": (None, [C.POINTER(sbd_engine_options)]),
+    "sbd_engine_create": (_int, [C.POINTER(_vp), C.POINTER(sbd_engine_options), _vp]),
+    "sbd_engine_destroy": (_int, [_vp]),
+    "sbd_engine_submit": (_int, [_vp, _int, _int, _int, _vp, _vp, _vp, _i64, _vp, _i64, _dbl, _dbl, _dbl, _int,
+                                 C.POINTER(_i64)]),
+    "sbd_engine_step": (_int, [_vp, C.POINTER(_int)]),
+    "sbd_engine_run": (_int, [_vp]),
+    "sbd_engine_result": (_int, [_vp, _i64, C.POINTER(sbd_job_result)]),
+    "sbd_engine_vector": (_int, [_vp, _i64, _vp, _i64]),
+    "sbd_engine_release": (_int, [_vp, _i64]),
+    "sbd_engine_get_stats": (_int, [_vp, C.POINTER(sbd_engine_stats)]),
+    "sbd_engine_clock": (_dbl, [_vp]),
 }
+
+SBD_PENDING = 2
 
 SBD_NOALLOC_MAX_STRINGS = 65536
 
@@ -283,6 +326,83 @@ def sbd_sort_strings_noalloc(keys, norb: int, nel: int, out, stream=None) -> tup
     return rc, bad.value
 
 
+def sbd_sigma_batched(handles, cs, sigmas, precision, rows_per_item: int = 0, stream=None) -> None:
+    """sigma of several instances in one batched launch sequence; handles, cs, sigmas: equal-length lists."""
+    n = len(handles)
+    if not (len(cs) == len(sigmas) == n):
+        raise ValueError("handles, cs and sigmas must have the same length")
+    hs = (C.c_void_p * max(n, 1))(*handles)
+    xs = (C.c_void_p * max(n, 1))(*[_ptr(x) for x in cs])
+    ys = (C.c_void_p * max(n, 1))(*[_ptr(y) for y in sigmas])
+    _check(load().sbd_sigma_batched(n, hs, xs, ys, PRECISION[precision], int(rows_per_item), _stream(stream)))
+
+
+def sbd_engine_default_options() -> sbd_engine_options:
+    o = sbd_engine_options()
+    load().sbd_engine_default_options(C.byref(o))
+    return o
+
+
+def sbd_engine_create(options: sbd_engine_options | None = None, stream=None) -> int:
+    out = C.c_void_p()
+    _check(load().sbd_engine_create(C.byref(out), C.byref(options) if options is not None else None,
+                                    _stream(stream)))
+    return out.value
+
+
+def sbd_engine_destroy(engine) -> None:
+    _check(load().sbd_engine_destroy(engine))
+
+
+def sbd_engine_submit(engine, norb, nalpha, nbeta, h, eri, A, B, ecore=0.0, tol=1e-6, tol_energy=0.0,
+                      keep_vector=False) -> int:
+    A = np.ascontiguousarray(A, dtype=np.uint64)
+    B = np.ascontiguousarray(B, dtype=np.uint64)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    job = C.c_int64()
+    _check(load().sbd_engine_submit(engine, int(norb), int(nalpha), int(nbeta), _ptr(h), _ptr(eri), _ptr(A),
+                                    int(A.size), _ptr(B), int(B.size), float(ecore), float(tol),
+                                    float(tol_energy), int(bool(keep_vector)), C.byref(job)))
+    return job.value
+
+
+def sbd_engine_step(engine) -> int:
+    rem = C.c_int()
+    _check(load().sbd_engine_step(engine, C.byref(rem)))
+    return rem.value
+
+
+def sbd_engine_run(engine) -> None:
+    _check(load().sbd_engine_run(engine))
+
+
+def sbd_engine_result(engine, job) -> tuple[int, sbd_job_result]:
+    r = sbd_job_result()
+    rc = load().sbd_engine_result(engine, int(job), C.byref(r))
+    _check(rc)
+    return rc, r
+
+
+def sbd_engine_vector(engine, job, out) -> None:
+    _check(load().sbd_engine_vector(engine, int(job), _ptr(out), int(out.size if isinstance(out, np.ndarray)
+                                                                      else out.numel())))
+
+
+def sbd_engine_release(engine, job) -> None:
+    _check(load().sbd_engine_release(engine, int(job)))
+
+
+def sbd_engine_get_stats(engine) -> sbd_engine_stats:
+    st = sbd_engine_stats()
+    _check(load().sbd_engine_get_stats(engine, C.byref(st)))
+    return st
+
+
+def sbd_engine_clock(engine) -> float:
+    return float(load().sbd_engine_clock(engine))
+
+
 def sbd_last_error(handle=None) -> str:
     m = load().sbd_last_error(handle)
     return m.decode() if m else ""
@@ -310,7 +430,8 @@ class SBD:
 
     def __init__(self, norb, nalpha, nbeta, h, eri, A, B, *, stream=None, allocator: str = "torch",
                  delta: float = 1e-4, max_subspace: int = 0, max_iter: int = 200, hbm_budget_bytes: int = 0,
-                 ecore: float = 0.0, table_algo: int = 0, verbose: int = 0, timing: bool = False):
+                 ecore: float = 0.0, table_algo: int = 0, verbose: int = 0, timing: bool = False,
+                 tol_energy: float = 0.0):
         self._opts = sbd_default_options()
         self._opts.delta = delta
         self._opts.max_subspace = max_subspace
@@ -320,6 +441,7 @@ class SBD:
         self._opts.table_algo = table_algo
         self._opts.verbose = verbose
         self._opts.timing = int(bool(timing))
+        self._opts.tol_energy = float(tol_energy)
         self._alloc = None
         if allocator == "torch":
             self._alloc = _TorchAllocator()
@@ -412,3 +534,73 @@ class SBD:
             v = torch.empty((nroots, self.N), dtype=torch.float64, pin_memory=True)
         rc, rep = sbd_davidson(self.handle, nroots, tol, precision, e, v, r)
         return SolveResult(e, r, v, rc, rep.as_dict())
+
+
+class Engine:
+    """Batched / served solver: jobs submitted here iterate together on the device."""
+
+    def __init__(self, *, max_slots=64, max_subspace=12, max_iter=200, max_norb=64, max_strings=20000,
+                 rows_per_item=0, delta=1e-4, hbm_budget_bytes=0, allocator: str = "torch", stream=None):
+        o = sbd_engine_default_options()
+        o.max_slots, o.max_subspace, o.max_iter = max_slots, max_subspace, max_iter
+        o.max_norb, o.max_strings, o.rows_per_item = max_norb, max_strings, rows_per_item
+        o.delta, o.hbm_budget_bytes = delta, hbm_budget_bytes
+        self._alloc = None
+        if allocator == "torch":
+            self._alloc = _TorchAllocator()
+            o.alloc, o.free = self._alloc.alloc, self._alloc.free
+        elif allocator != "cuda":
+            raise ValueError("allocator must be 'torch' or 'cuda'")
+        self._opts = o
+        self.engine = None
+        self.engine = sbd_engine_create(o, stream)
+
+    def submit(self, wl_or_norb, *args, tol=1e-6, tol_energy=0.0, keep_vector=False, ecore=0.0) -> int:
+        """submit(workload) or submit(norb, nalpha, nbeta, h, eri, A, B)."""
+        if args:
+            norb, (nalpha, nbeta, h, eri, A, B) = wl_or_norb, args
+        else:
+            w = wl_or_norb
+            norb, nalpha, nbeta, h, eri, A, B = w.norb, w.nalpha, w.nbeta, w.h, w.eri, w.A, w.B
+        return sbd_engine_submit(self.engine, norb, nalpha, nbeta, h, eri, A, B, ecore, tol, tol_energy, keep_vector)
+
+    def step(self) -> int:
+        return sbd_engine_step(self.engine)
+
+    def run(self) -> None:
+        sbd_engine_run(self.engine)
+
+    def result(self, job) -> dict | None:
+        rc, r = sbd_engine_result(self.engine, job)
+        return None if rc == SBD_PENDING else r.as_dict()
+
+    def vector(self, job, n) -> np.ndarray:
+        out = np.empty(int(n), dtype=np.float64)
+        sbd_engine_vector(self.engine, job, out)
+        return out
+
+    def release(self, job) -> None:
+        sbd_engine_release(self.engine, job)
+
+    def stats(self) -> dict:
+        return sbd_engine_get_stats(self.engine).as_dict()
+
+    def clock(self) -> float:
+        return sbd_engine_clock(self.engine)
+
+    def close(self):
+        if self.engine:
+            sbd_engine_destroy(self.engine)
+            self.engine = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

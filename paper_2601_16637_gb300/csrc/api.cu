@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <atomic>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
@@ -113,6 +114,8 @@ struct sbd_ctx {
     Ctx c;
 };
 
+Ctx &sbd::ctx_of(sbd_handle h) { return h->c; }
+
 static thread_local std::string g_last_error;
 
 void sbd::set_thread_error(const std::string &msg) { g_last_error = msg; }
@@ -153,6 +156,7 @@ const char *sbd_status_string(int status)
     switch (status) {
     case SBD_OK: return "ok";
     case SBD_NOT_CONVERGED: return "not converged";
+    case SBD_PENDING: return "pending";
     case SBD_ERR_INVALID_ARG: return "invalid argument";
     case SBD_ERR_BAD_STRING: return "bad string";
     case SBD_ERR_DUPLICATE_STRING: return "duplicate string";
@@ -165,6 +169,54 @@ const char *sbd_status_string(int status)
     case SBD_ERR_UNSUPPORTED: return "unsupported size";
     default: return "unknown status";
     }
+}
+
+int sbd_sigma_batched(int n, const sbd_handle *handles, const void *const *c_dev, double *const *sigma_dev,
+                      sbd_precision prec, int rows_per_item, void *stream)
+{
+    if (n < 0 || (n > 0 && (!handles || !c_dev || !sigma_dev)) || (prec != SBD_FP64 && prec != SBD_MIXED)) {
+        g_last_error = "sbd_sigma_batched: invalid argument";
+        return SBD_ERR_INVALID_ARG;
+    }
+    if (n == 0) return SBD_OK;
+    return guarded(nullptr, [&]() -> int {
+        cudaStream_t s = (cudaStream_t)stream;
+        int max_strings = 1, max_norb = 1, device = 0;
+        std::vector<SigmaSlot> slots((size_t)n);
+        for (int i = 0; i < n; ++i) {
+            if (!handles[i] || !c_dev[i] || !sigma_dev[i]) fail(SBD_ERR_INVALID_ARG, "sbd_sigma_batched: NULL entry");
+            for (int j = 0; j < i; ++j)
+                if (handles[j] == handles[i]) fail(SBD_ERR_INVALID_ARG, "sbd_sigma_batched: a handle appears twice");
+            Ctx &c = handles[i]->c;
+            if (i == 0) device = c.device;
+            else if (c.device != device) fail(SBD_ERR_INVALID_ARG, "sbd_sigma_batched: handles on different devices");
+            max_strings = (int)std::max<int64_t>(max_strings, std::max(c.nA, c.nB));
+            max_norb = std::max(max_norb, c.norb);
+            slots[i] = SigmaSlot{&c, c_dev[i], sigma_dev[i], nullptr, c.work_t};
+        }
+        int R = rows_per_item;
+        if (R == 0) {
+            for (int cand : {4, 2, 1}) {
+                if (cand == 4 && prec == SBD_FP64) continue;
+                if (sigma_batch_smem(prec, cand, max_strings, max_norb) <= sigma_batch_smem_limit(device)) {
+                    R = cand;
+                    break;
+                }
+            }
+            if (R == 0) fail(SBD_ERR_UNSUPPORTED, "sbd_sigma_batched: string sets too large for the staged passes");
+        }
+        SigmaBatch *b = sigma_batch_create(n, prec, R, max_strings, max_norb, device);
+        try {
+            sigma_batch_set(b, slots.data(), n);
+            sigma_batch_launch(b, s);
+            SBD_CUDA(cudaStreamSynchronize(s));
+        } catch (...) {
+            sigma_batch_destroy(b);
+            throw;
+        }
+        sigma_batch_destroy(b);
+        return SBD_OK;
+    });
 }
 
 const char *sbd_last_error(sbd_handle h) { return h ? h->c.last_error.c_str() : g_last_error.c_str(); }

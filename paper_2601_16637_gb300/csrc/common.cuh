@@ -107,6 +107,9 @@ struct Ctx {
     int64_t kernel_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
+// the context inside a C-ABI handle (api.cu)
+Ctx &ctx_of(sbd_handle h);
+
 // kernel timing helpers (api.cu)
 cudaEvent_t take_event(Ctx &c);
 void harvest_timing(Ctx &c);
@@ -167,6 +170,33 @@ void to_float(const double *in, float *out, int64_t n, cudaStream_t s);
 
 // sigma.cu
 void sigma_prepare(Ctx &c);
+
+// ---------------------------------------------------------------------------
+// batched sigma: many instances in one set of persistent launches (sigma.cu)
+
+// One instance of a batched sigma (host side).
+struct SigmaSlot {
+    const Ctx *c;
+    const void *x;       // amplitudes [nA][nB]: float (mixed) or double (FP64)
+    double *y;           // sigma [nA][nB], overwritten
+    const double *x64;   // mixed only: FP64 amplitudes for the diagonal term, or null
+    void *xt;            // [nA*nB] elements of the precision: transposed copy of x
+};
+struct SigmaBatch;
+// Device descriptors for up to max_slots instances whose string sets have at most max_strings
+// entries per spin and norb <= max_norb; R = rows staged per work item (1, 2 or 4 (FP32 only)).
+SigmaBatch *sigma_batch_create(int max_slots, sbd_precision prec, int R, int max_strings, int max_norb, int device);
+// Shared memory one work item needs with R staged rows; compare with sigma_batch_smem_limit().
+size_t sigma_batch_smem(sbd_precision prec, int R, int max_strings, int max_norb);
+size_t sigma_batch_smem_limit(int device);
+// Fills the host staging copy of the descriptors (no device work).
+void sigma_batch_set(SigmaBatch *b, const SigmaSlot *slots, int n);
+// Copies the staged descriptors to the device and runs transpose, beta, alpha and alpha-beta
+// passes over every slot: fixed grids and device-resident counts, so the sequence can be
+// captured in a CUDA graph once and replayed after each sigma_batch_set.
+void sigma_batch_launch(SigmaBatch *b, cudaStream_t s);
+void sigma_batch_destroy(SigmaBatch *b);
+int64_t sigma_batch_launches(const SigmaBatch *b);  // kernel launches per sigma_batch_launch
 // c64 (mixed only, may be NULL): the FP64 amplitudes, used for the diagonal term
 void sigma_apply(Ctx &c, const void *cvec, double *svec, sbd_precision prec, cudaStream_t s,
                  const double *c64 = nullptr);

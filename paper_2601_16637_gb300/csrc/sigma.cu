@@ -181,11 +181,13 @@ struct RowArgs {
 
 // Gather pass over rows of X: each CTA stages R consecutive rows, then every
 // output column c sums its excitation list (column spin) inside those rows.
+// row_group() does one group of rows starting at r0; the single-instance
+// kernel strides over the groups, the batched kernel takes (instance, group)
+// items from a work counter.
 template <typename T, int R, bool STAGED>
-__global__ void __launch_bounds__(Threads<T>::value) row_pass_kernel(const RowArgs<T> a)
+__device__ __forceinline__ void row_group(const RowArgs<T> &a, int64_t r0, unsigned char *smem)
 {
     constexpr int kThreads = Threads<T>::value;
-    extern __shared__ __align__(16) unsigned char smem[];
     const int n2 = a.norb * a.norb;
     const size_t xs_bytes = STAGED ? round16((size_t)a.ncol * R * sizeof(T)) : 0;
     T *Xs = reinterpret_cast<T *>(smem);
@@ -193,8 +195,7 @@ __global__ void __launch_bounds__(Threads<T>::value) row_pass_kernel(const RowAr
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gi = lane / kGroup, lig = lane % kGroup;
     const int64_t ngroups = (kThreads / 32) * kGroupsPerWarp;
-
-    for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < a.nrow; r0 += (int64_t)gridDim.x * R) {
+    {
         const int nr = (int)min((int64_t)R, a.nrow - r0);
         __syncthreads();
         if (STAGED) {
@@ -293,6 +294,13 @@ __global__ void __launch_bounds__(Threads<T>::value) row_pass_kernel(const RowAr
     }
 }
 
+template <typename T, int R, bool STAGED>
+__global__ void __launch_bounds__(Threads<T>::value) row_pass_kernel(const RowArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < a.nrow; r0 += (int64_t)gridDim.x * R) row_group<T, R, STAGED>(a, r0, smem);
+}
+
 template <typename T>
 struct AbArgs {
     const T *C;  // [nA][nB]
@@ -313,10 +321,9 @@ struct AbArgs {
 // and adds acc to s(ia, ib) with a fire-and-forget reduction (the same thread
 // owns (ia, ib) for every group of this row, so the adds land in program order).
 template <typename T, int R, bool STAGED>
-__global__ void __launch_bounds__(Threads<T>::value) ab_pass_kernel(const AbArgs<T> a)
+__device__ __forceinline__ void ab_row(const AbArgs<T> &a, int64_t ia, unsigned char *smem)
 {
     constexpr int kThreads = Threads<T>::value;
-    extern __shared__ __align__(16) unsigned char smem[];
     const int n2 = a.norb * a.norb;
     const size_t cs_bytes = STAGED ? round16((size_t)a.nB * R * sizeof(T)) : 0;
     T *Cs = reinterpret_cast<T *>(smem);
@@ -324,8 +331,7 @@ __global__ void __launch_bounds__(Threads<T>::value) ab_pass_kernel(const AbArgs
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gi = lane / kGroup, lig = lane % kGroup;
     const int64_t ngroups = (kThreads / 32) * kGroupsPerWarp;
-
-    for (int64_t ia = blockIdx.x; ia < a.nA; ia += gridDim.x) {
+    {
         const int64_t e0 = a.as_ptr[ia];
         const int K = (int)(a.as_ptr[ia + 1] - e0);
         for (int k0 = 0; k0 < K; k0 += R) {
@@ -408,6 +414,13 @@ __global__ void __launch_bounds__(Threads<T>::value) ab_pass_kernel(const AbArgs
             }
         }
     }
+}
+
+template <typename T, int R, bool STAGED>
+__global__ void __launch_bounds__(Threads<T>::value) ab_pass_kernel(const AbArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int64_t ia = blockIdx.x; ia < a.nA; ia += gridDim.x) ab_row<T, R, STAGED>(a, ia, smem);
 }
 
 // out[c][r] = in[r][c]
@@ -532,18 +545,14 @@ void timed(Ctx &c, int slot, cudaStream_t s, F &&launch)
     c.pending.push_back({slot, a, b});
 }
 
+// Arguments of the three gather passes of one instance: beta pass on C, alpha pass on its
+// transpose Ct, alpha-beta pass on C (the single-instance and the batched launches share them).
 template <typename T>
-void apply(Ctx &c, const T *C, double *S, const double *c64, cudaStream_t s)
+void make_args(const Ctx &c, const T *C, double *S, const double *c64, const T *Ct, RowArgs<T> &rb, RowArgs<T> &ra,
+               AbArgs<T> &ab)
 {
-    const int n2 = c.norb * c.norb;
-    const int rmax = sizeof(T) == 4 ? 4 : 2;
-    const size_t lim = smem_limit(c);
     const SpinTables &ta = c.sp[0], &tb = c.sp[1];
-    const int base = sizeof(T) == 4 ? 4 : 0;
-    T *Ct = static_cast<T *>(c.work_t);
-    timed(c, base + 0, s, [&] { transpose<T>(C, Ct, c.nA, c.nB, s); });
-
-    RowArgs<T> rb{};
+    rb = RowArgs<T>{};
     rb.X = C;
     rb.nrow = c.nA;
     rb.ncol = c.nB;
@@ -559,9 +568,8 @@ void apply(Ctx &c, const T *C, double *S, const double *c64, cudaStream_t s)
     rb.s_ptr = tb.sig_s_ptr;
     rb.d_ptr = tb.sig_d_ptr;
     rb.lists = lists_of<T>(tb);
-    timed(c, base + 1, s, [&] { launch_row<T>(rb, choose(c.nB, n2, sizeof(T), rmax, lim), s); });
 
-    RowArgs<T> ra = rb;
+    ra = rb;
     ra.X = Ct;
     ra.nrow = c.nB;
     ra.ncol = c.nA;
@@ -574,9 +582,8 @@ void apply(Ctx &c, const T *C, double *S, const double *c64, cudaStream_t s)
     ra.s_ptr = ta.sig_s_ptr;
     ra.d_ptr = ta.sig_d_ptr;
     ra.lists = lists_of<T>(ta);
-    timed(c, base + 2, s, [&] { launch_row<T>(ra, choose(c.nA, n2, sizeof(T), rmax, lim), s); });
 
-    AbArgs<T> ab{};
+    ab = AbArgs<T>{};
     ab.C = C;
     ab.S = S;
     ab.nA = c.nA;
@@ -587,7 +594,235 @@ void apply(Ctx &c, const T *C, double *S, const double *c64, cudaStream_t s)
     ab.as_pk = ta.s_pk;
     ab.bs_ptr = tb.sig_s_ptr;  // padded beta lists for 16-byte loads
     ab.bs_pk = tb.s_pk_sig;
+}
+
+template <typename T>
+void apply(Ctx &c, const T *C, double *S, const double *c64, cudaStream_t s)
+{
+    const int n2 = c.norb * c.norb;
+    const int rmax = sizeof(T) == 4 ? 4 : 2;
+    const size_t lim = smem_limit(c);
+    const int base = sizeof(T) == 4 ? 4 : 0;
+    T *Ct = static_cast<T *>(c.work_t);
+    timed(c, base + 0, s, [&] { transpose<T>(C, Ct, c.nA, c.nB, s); });
+    RowArgs<T> rb, ra;
+    AbArgs<T> ab;
+    make_args<T>(c, C, S, c64, Ct, rb, ra, ab);
+    timed(c, base + 1, s, [&] { launch_row<T>(rb, choose(c.nB, n2, sizeof(T), rmax, lim), s); });
+    timed(c, base + 2, s, [&] { launch_row<T>(ra, choose(c.nA, n2, sizeof(T), rmax, lim), s); });
     timed(c, base + 3, s, [&] { launch_ab<T>(ab, choose(c.nB, n2, sizeof(T), rmax, lim), s); });
+}
+
+// ---------------------------------------------------------------------------
+// Batched sigma.  One descriptor block holds, for every slot, the arguments of its passes and
+// the prefix sums of its work items (transpose tiles, beta row groups, alpha row groups, alpha-beta
+// rows).  Persistent CTAs take items from a counter and run the same per-item device functions as
+// the single-instance kernels, so every output element is computed by the same arithmetic.
+
+template <typename T>
+struct TDesc {
+    const T *in;
+    T *out;
+    int64_t rows, cols;
+};
+
+struct Layout {
+    size_t n, off_t, off_b, off_a, off_ab, td, rb, ra, ab, total;
+};
+
+template <typename T>
+Layout layout_for(int m)
+{
+    Layout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = (o + bytes + 255) & ~(size_t)255;
+        return at;
+    };
+    L.n = take(sizeof(int));
+    L.off_t = take(sizeof(int64_t) * (m + 1));
+    L.off_b = take(sizeof(int64_t) * (m + 1));
+    L.off_a = take(sizeof(int64_t) * (m + 1));
+    L.off_ab = take(sizeof(int64_t) * (m + 1));
+    L.td = take(sizeof(TDesc<T>) * m);
+    L.rb = take(sizeof(RowArgs<T>) * m);
+    L.ra = take(sizeof(RowArgs<T>) * m);
+    L.ab = take(sizeof(AbArgs<T>) * m);
+    L.total = o;
+    return L;
+}
+
+// slot s with off[s] <= item < off[s + 1] (empty slots are skipped)
+__device__ __forceinline__ int find_slot(const int64_t *off, int n, int64_t item)
+{
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= item) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename T>
+__global__ void transpose_batch_kernel(const int *pn, const int64_t *off, const TDesc<T> *td)
+{
+    __shared__ T tile[32][33];
+    const int n = *pn;
+    const int64_t total = off[n];
+    for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
+        const int sl = find_slot(off, n, it);
+        const TDesc<T> d = td[sl];
+        const int64_t lt = it - off[sl], tx = (d.cols + 31) / 32;
+        const int64_t by = (lt / tx) * 32, bx = (lt % tx) * 32;
+        __syncthreads();
+        for (int j = threadIdx.y; j < 32; j += 8) {
+            const int64_t r = by + j, c = bx + threadIdx.x;
+            if (r < d.rows && c < d.cols) tile[j][threadIdx.x] = d.in[r * d.cols + c];
+        }
+        __syncthreads();
+        for (int j = threadIdx.y; j < 32; j += 8) {
+            const int64_t c = bx + j, r = by + threadIdx.x;
+            if (r < d.rows && c < d.cols) d.out[c * d.rows + r] = tile[threadIdx.x][j];
+        }
+    }
+}
+
+// Work-item loop of the persistent pass kernels: thread 0 takes the next item from the counter,
+// the CTA copies the slot's arguments to shared memory when the slot changes, then runs body().
+template <typename Args, typename F>
+__device__ __forceinline__ void item_loop(const int *pn, const int64_t *off, const Args *args,
+                                          unsigned long long *counter, Args &sa, F &&body)
+{
+    __shared__ int64_t s_item;
+    __shared__ int s_slot;
+    const int n = *pn;
+    const int64_t total = off[n];
+    int cur = -1;
+    while (true) {
+        __syncthreads();  // the previous item is finished with shared memory
+        if (threadIdx.x == 0) {
+            const int64_t it = (int64_t)atomicAdd(counter, 1ull);
+            s_item = it;
+            s_slot = it < total ? find_slot(off, n, it) : -1;
+        }
+        __syncthreads();
+        const int64_t it = s_item;
+        const int sl = s_slot;
+        if (it >= total) break;
+        if (sl != cur) {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(args + sl);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&sa);
+            for (int i = threadIdx.x; i < (int)(sizeof(Args) / 4); i += blockDim.x) dst[i] = src[i];
+            cur = sl;
+            __syncthreads();
+        }
+        body(it - off[sl]);
+    }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(Threads<T>::value) row_batch_kernel(const int *pn, const int64_t *off,
+                                                                      const RowArgs<T> *args,
+                                                                      unsigned long long *counter)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ RowArgs<T> sa;
+    item_loop(pn, off, args, counter, sa, [&](int64_t li) { row_group<T, R, true>(sa, li * R, smem); });
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(Threads<T>::value) ab_batch_kernel(const int *pn, const int64_t *off,
+                                                                     const AbArgs<T> *args,
+                                                                     unsigned long long *counter)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ AbArgs<T> sa;
+    item_loop(pn, off, args, counter, sa, [&](int64_t li) { ab_row<T, R, true>(sa, li, smem); });
+}
+
+size_t batch_smem(size_t elem, int R, int max_strings, int max_norb)
+{
+    return round16((size_t)max_strings * R * elem) + (size_t)2 * max_norb * max_norb * R * elem;
+}
+
+}  // namespace
+
+struct SigmaBatch {
+    sbd_precision prec = SBD_MIXED;
+    int max_slots = 0, R = 1, device = 0, grid_pass = 0, grid_t = 0;
+    size_t smem = 0;
+    Layout L{};
+    unsigned char *dev = nullptr, *host = nullptr;
+    unsigned long long *counters = nullptr;  // [3]: beta, alpha, alpha-beta
+};
+
+namespace {
+
+template <typename T>
+void batch_set(SigmaBatch *b, const SigmaSlot *slots, int n)
+{
+    const Layout &L = b->L;
+    unsigned char *h = b->host;
+    *reinterpret_cast<int *>(h + L.n) = n;
+    int64_t *ot = reinterpret_cast<int64_t *>(h + L.off_t), *ob = reinterpret_cast<int64_t *>(h + L.off_b);
+    int64_t *oa = reinterpret_cast<int64_t *>(h + L.off_a), *oab = reinterpret_cast<int64_t *>(h + L.off_ab);
+    TDesc<T> *td = reinterpret_cast<TDesc<T> *>(h + L.td);
+    RowArgs<T> *rb = reinterpret_cast<RowArgs<T> *>(h + L.rb), *ra = reinterpret_cast<RowArgs<T> *>(h + L.ra);
+    AbArgs<T> *ab = reinterpret_cast<AbArgs<T> *>(h + L.ab);
+    ot[0] = ob[0] = oa[0] = oab[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        const SigmaSlot &sl = slots[i];
+        const Ctx &c = *sl.c;
+        const T *x = static_cast<const T *>(sl.x);
+        T *xt = static_cast<T *>(sl.xt);
+        make_args<T>(c, x, sl.y, sl.x64, xt, rb[i], ra[i], ab[i]);
+        td[i] = TDesc<T>{x, xt, c.nA, c.nB};
+        ot[i + 1] = ot[i] + ((c.nA + 31) / 32) * ((c.nB + 31) / 32);
+        ob[i + 1] = ob[i] + (c.nA + b->R - 1) / b->R;
+        oa[i + 1] = oa[i] + (c.nB + b->R - 1) / b->R;
+        oab[i + 1] = oab[i] + c.nA;
+    }
+}
+
+template <typename T, int R>
+void batch_launch_r(SigmaBatch *b, cudaStream_t s)
+{
+    constexpr int kThreads = Threads<T>::value;
+    const Layout &L = b->L;
+    unsigned char *d = b->dev;
+    const int *pn = reinterpret_cast<const int *>(d + L.n);
+    transpose_batch_kernel<T><<<b->grid_t, dim3(32, 8), 0, s>>>(pn, reinterpret_cast<const int64_t *>(d + L.off_t),
+                                                                reinterpret_cast<const TDesc<T> *>(d + L.td));
+    SBD_LAUNCH("transpose_batch_kernel");
+    row_batch_kernel<T, R><<<b->grid_pass, kThreads, b->smem, s>>>(
+        pn, reinterpret_cast<const int64_t *>(d + L.off_b), reinterpret_cast<const RowArgs<T> *>(d + L.rb), b->counters);
+    SBD_LAUNCH("row_batch_kernel");
+    row_batch_kernel<T, R><<<b->grid_pass, kThreads, b->smem, s>>>(
+        pn, reinterpret_cast<const int64_t *>(d + L.off_a), reinterpret_cast<const RowArgs<T> *>(d + L.ra),
+        b->counters + 1);
+    SBD_LAUNCH("row_batch_kernel");
+    ab_batch_kernel<T, R><<<b->grid_pass, kThreads, b->smem, s>>>(
+        pn, reinterpret_cast<const int64_t *>(d + L.off_ab), reinterpret_cast<const AbArgs<T> *>(d + L.ab),
+        b->counters + 2);
+    SBD_LAUNCH("ab_batch_kernel");
+}
+
+template <typename T, int R>
+void batch_attrs(SigmaBatch *b)
+{
+    constexpr int kThreads = Threads<T>::value;
+    SBD_CUDA(cudaFuncSetAttribute(row_batch_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    SBD_CUDA(cudaFuncSetAttribute(ab_batch_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    int occ_row = 0, occ_ab = 0;
+    SBD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_row, row_batch_kernel<T, R>, kThreads, b->smem));
+    SBD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ab, ab_batch_kernel<T, R>, kThreads, b->smem));
+    const int occ = std::max(1, std::min(occ_row, occ_ab));
+    int sms = 0;
+    SBD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    b->grid_pass = sms * occ;
+    b->grid_t = sms * 8;
 }
 
 }  // namespace
@@ -596,6 +831,92 @@ void sigma_prepare(Ctx &c)
 {
     set_attrs<double>(c.smem_optin);
     set_attrs<float>(c.smem_optin);
+}
+
+size_t sigma_batch_smem(sbd_precision prec, int R, int max_strings, int max_norb)
+{
+    return batch_smem(prec == SBD_FP64 ? 8 : 4, R, max_strings, max_norb);
+}
+
+size_t sigma_batch_smem_limit(int device)
+{
+    int optin = 0;
+    SBD_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    return (size_t)optin - 1024;  // headroom for the kernels' static shared memory
+}
+
+SigmaBatch *sigma_batch_create(int max_slots, sbd_precision prec, int R, int max_strings, int max_norb, int device)
+{
+    if (max_slots < 1) fail(SBD_ERR_INVALID_ARG, "batched sigma needs at least one slot");
+    if (!(R == 1 || R == 2 || (R == 4 && prec == SBD_MIXED)))
+        fail(SBD_ERR_INVALID_ARG, "rows per work item must be 1, 2 or (mixed only) 4");
+    const size_t smem = sigma_batch_smem(prec, R, max_strings, max_norb);
+    if (smem > sigma_batch_smem_limit(device))
+        fail(SBD_ERR_UNSUPPORTED, "batched sigma: staged rows do not fit in shared memory");
+    auto *b = new SigmaBatch();
+    b->prec = prec;
+    b->max_slots = max_slots;
+    b->R = R;
+    b->device = device;
+    b->smem = smem;
+    b->L = prec == SBD_FP64 ? layout_for<double>(max_slots) : layout_for<float>(max_slots);
+    try {
+        SBD_CUDA(cudaMalloc(&b->dev, b->L.total));
+        SBD_CUDA(cudaMallocHost(&b->host, b->L.total));
+        SBD_CUDA(cudaMalloc(&b->counters, 3 * sizeof(unsigned long long)));
+        memset(b->host, 0, b->L.total);
+        if (prec == SBD_FP64) {
+            if (R == 2) batch_attrs<double, 2>(b);
+            else batch_attrs<double, 1>(b);
+        } else {
+            if (R == 4) batch_attrs<float, 4>(b);
+            else if (R == 2) batch_attrs<float, 2>(b);
+            else batch_attrs<float, 1>(b);
+        }
+    } catch (...) {
+        sigma_batch_destroy(b);
+        throw;
+    }
+    return b;
+}
+
+void sigma_batch_set(SigmaBatch *b, const SigmaSlot *slots, int n)
+{
+    if (n < 0 || n > b->max_slots) fail(SBD_ERR_INVALID_ARG, "batched sigma: too many slots");
+    const int lim_n2 = 0;
+    (void)lim_n2;
+    for (int i = 0; i < n; ++i) {
+        const Ctx &c = *slots[i].c;
+        if (sigma_batch_smem(b->prec, b->R, (int)std::max(c.nA, c.nB), c.norb) > b->smem)
+            fail(SBD_ERR_UNSUPPORTED, "batched sigma: an instance exceeds the string or orbital limit of the batch");
+    }
+    if (b->prec == SBD_FP64) batch_set<double>(b, slots, n);
+    else batch_set<float>(b, slots, n);
+}
+
+void sigma_batch_launch(SigmaBatch *b, cudaStream_t s)
+{
+    SBD_CUDA(cudaMemcpyAsync(b->dev, b->host, b->L.total, cudaMemcpyHostToDevice, s));
+    SBD_CUDA(cudaMemsetAsync(b->counters, 0, 3 * sizeof(unsigned long long), s));
+    if (b->prec == SBD_FP64) {
+        if (b->R == 2) batch_launch_r<double, 2>(b, s);
+        else batch_launch_r<double, 1>(b, s);
+    } else {
+        if (b->R == 4) batch_launch_r<float, 4>(b, s);
+        else if (b->R == 2) batch_launch_r<float, 2>(b, s);
+        else batch_launch_r<float, 1>(b, s);
+    }
+}
+
+int64_t sigma_batch_launches(const SigmaBatch *) { return 4; }
+
+void sigma_batch_destroy(SigmaBatch *b)
+{
+    if (!b) return;
+    if (b->dev) (void)cudaFree(b->dev);
+    if (b->host) (void)cudaFreeHost(b->host);
+    if (b->counters) (void)cudaFree(b->counters);
+    delete b;
 }
 
 void sigma_apply(Ctx &c, const void *cvec, double *svec, sbd_precision prec, cudaStream_t s, const double *c64)

@@ -183,6 +183,56 @@ CONFIGS = {
 }
 
 
+def batch_instances(n: int = 64, seed: int = 4, lam: float = 0.35, tol: float = 1e-3,
+                    tol_energy: float = 1e-6) -> list[Workload]:
+    """The batched workload: n independent instances, norb uniform in {16, 20, 24, 26},
+    nalpha = nbeta = round(norb / 3), |A| and |B| uniform in [500, 5000] (clamped to the full
+    string space), each with its own seeded integrals.  tol / tol_energy: the residual and
+    Ritz-value-change thresholds that stand for "1e-6 Ha"."""
+    rng = np.random.default_rng([seed, 200])
+    out = []
+    for i in range(n):
+        norb = int(rng.choice([16, 20, 24, 26]))
+        nel = int(round(norb / 3))
+        full = math.comb(norb, nel)
+        nA = min(int(rng.integers(500, 5001)), full)
+        nB = min(int(rng.integers(500, 5001)), full)
+        wl = make(f"batch{n}-{i}", norb, nel, nel, nA, nB, lam, seed=1000 * seed + i, nroots=1, tol=tol,
+                  precision="mixed")
+        wl.extra["tol_energy"] = tol_energy
+        out.append(wl)
+    return out
+
+
+def serving_trace(n: int = 200, rate: float = 20.0, seed: int = 5, lam: float = 0.35, tol: float = 1e-3,
+                  tol_energy: float = 1e-6, max_strings: int = 20000, min_strings: int = 300,
+                  norbs=(24, 32, 40, 48, 58)) -> list[tuple[float, Workload]]:
+    """The serving workload: a finite Poisson stream of n jobs at `rate` per second.  Each job has
+    norb uniform in `norbs`, nalpha = nbeta = round(norb / 3), |A| = |B| log-uniform in
+    [min_strings, max_strings] and its own seeded integrals.  Returns (arrival time s, job) pairs
+    in arrival order; the instances are built lazily by the caller through `make_job`."""
+    rng = np.random.default_rng([seed, 300])
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        norb = int(rng.choice(list(norbs)))
+        nel = int(round(norb / 3))
+        ns = int(round(math.exp(rng.uniform(math.log(min_strings), math.log(max_strings)))))
+        ns = min(ns, math.comb(norb, nel))
+        spec = dict(name=f"serve-{i}", norb=norb, nalpha=nel, nbeta=nel, nA=ns, nB=ns, lam=lam,
+                    seed=1000 * seed + i, nroots=1, tol=tol, precision="mixed")
+        out.append((t, spec, tol_energy))
+    return out
+
+
+def make_job(spec: dict, tol_energy: float) -> Workload:
+    """Builds one serving job from its spec (see serving_trace)."""
+    wl = make(**spec)
+    wl.extra["tol_energy"] = tol_energy
+    return wl
+
+
 def config(name: str, **override) -> Workload:
     spec = dict(CONFIGS[name])
     spec.update(override)

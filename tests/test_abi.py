@@ -34,9 +34,61 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_struct_layouts_match_header():
-    # sbd_options: double, int, int, size_t, double, int, int, fn, fn, void*, int (+4 padding)  (LP64)
-    assert ctypes.sizeof(b.sbd_options) == 8 + 4 + 4 + 8 + 8 + 4 + 4 + 8 + 8 + 8 + 4 + 4
+    # sbd_options: double, int, int, size_t, double, int, int, fn, fn, void*, int (+4 padding), double
+    assert ctypes.sizeof(b.sbd_options) == 8 + 4 + 4 + 8 + 8 + 4 + 4 + 8 + 8 + 8 + 4 + 4 + 8
     assert ctypes.sizeof(b.sbd_report) == 7 * 4 + 4 + 3 * 8  # 7 ints, padding, 3 doubles
+
+
+def test_struct_layouts_match_the_compiled_header(tmp_path):
+    """sizeof and every field offset of the header's structs, as the C compiler lays them out, equal
+    the binding's ctypes mirrors."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"sbd_options": b.sbd_options, "sbd_report": b.sbd_report,
+               "sbd_engine_options": b.sbd_engine_options, "sbd_job_result": b.sbd_job_result,
+               "sbd_engine_stats": b.sbd_engine_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sbd.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.split("\n") if l)
+    for name, cls in structs.items():
+        assert int(out[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(out[f"{name}.{f}"]) == getattr(cls, f).offset, f"{name}.{f}"
+
+
+def test_engine_defaults_and_argument_errors_need_no_gpu(lib):
+    o = b.sbd_engine_default_options()
+    assert (o.max_slots, o.max_subspace, o.max_iter, o.max_norb, o.max_strings) == (64, 12, 200, 64, 20000)
+    assert o.rows_per_item == 0 and o.delta == 1e-4 and o.hbm_budget_bytes == 0
+    out = ctypes.c_void_p()
+    bad = b.sbd_engine_default_options()
+    bad.max_subspace = 33
+    assert lib.sbd_engine_create(ctypes.byref(out), ctypes.byref(bad), None) == -1
+    bad = b.sbd_engine_default_options()
+    bad.rows_per_item = 3
+    assert lib.sbd_engine_create(ctypes.byref(out), ctypes.byref(bad), None) == -1
+    assert lib.sbd_engine_create(None, None, None) == -1
+    assert lib.sbd_engine_destroy(None) == -1
+    assert lib.sbd_engine_step(None, None) == -1
+    assert lib.sbd_engine_run(None) == -1
+    r = b.sbd_job_result()
+    assert lib.sbd_engine_result(None, 0, ctypes.byref(r)) == -1
+    assert lib.sbd_sigma_batched(-1, None, None, None, 0, 0, None) == -1
+    assert lib.sbd_sigma_batched(0, None, None, None, 0, 0, None) == 0
+    assert b.sbd_status_string(2) == "pending"
 
 
 def test_defaults_and_status_strings(lib):
