@@ -251,7 +251,7 @@ def run_batch(args):
 
     B.load(build_if_missing=True)
     insts = W.batch_instances(args.batch_n)
-    opts = dict(max_slots=len(insts), max_subspace=12, max_norb=26, max_strings=5000)
+    opts = dict(max_slots=len(insts), max_subspace=args.engine_subspace, max_norb=26, max_strings=5000)
     small = sorted(insts, key=lambda w: w.ndets)[:2]
     for _ in range(args.warmup):
         with B.Engine(**opts) as e:
@@ -274,26 +274,32 @@ def run_batch(args):
         dets_sigma += sum(r["ndets"] * (r["sigma_mixed"] + r["sigma_fp64"]) for r in results)
     clk = clocks.stop()
     stream = torch.cuda.current_stream()
-    serial_t, dE, serial_status = 0.0, 0.0, []
+    serial_t, dE, serial_status, serial_it = 0.0, 0.0, [], []
     for w, r in zip(insts, results):
-        t, e64, st, _ = serial_fp64(B, w, stream)
+        t, e64, st, rep = serial_fp64(B, w, stream)
         serial_t += t
         serial_status.append(st)
+        serial_it.append(rep["iterations"])
         dE = max(dE, abs(e64 - r["energy"]))
     per_run = elapsed / args.steps
     extra = {"batch": {"instances": len(insts), "total_dets": int(sum(w.ndets for w in insts)),
                        "status_counts": {str(k): sum(1 for r in results if r["status"] == k)
                                          for k in sorted({r["status"] for r in results})},
-                       "iterations_mean": float(np.mean([r["iterations"] for r in results])),
+                       "iterations_min_median_max": [int(np.min([r["iterations"] for r in results])),
+                                                     float(np.median([r["iterations"] for r in results])),
+                                                     int(np.max([r["iterations"] for r in results]))],
+                       "max_subspace": args.engine_subspace,
                        "seconds_per_batch": per_run},
              "vs_serial_fp64": {"seconds": serial_t, "solves_per_s": len(insts) / serial_t,
+                                "iterations_min_median_max": [int(np.min(serial_it)), float(np.median(serial_it)),
+                                                              int(np.max(serial_it))],
                                 "speedup": serial_t / per_run, "max_abs_dE_Ha": dE,
                                 "statuses": {str(k): serial_status.count(k) for k in sorted(set(serial_status))}}}
     config = {"workload": f"batch{len(insts)}: {len(insts)} instances, norb in {{16,20,24,26}}, "
                           f"nalpha=nbeta=round(norb/3), |A|,|B| uniform in [500,5000], own integrals each; "
-                          f"1 root, mixed sigma, residual <= 1e-3 and Ritz-value change <= 1e-6 Ha",
+                          f"1 root, mixed sigma, residual <= {insts[0].tol:g} and Ritz-value change <= 1e-6 Ha",
               "step": "one engine run over all instances (admission, tables, Davidson, FP64 check)",
-              "max_subspace": 12, "rows_per_item": stats["rows_per_item"],
+              "max_subspace": args.engine_subspace, "rows_per_item": stats["rows_per_item"],
               "l2": "inputs larger than L2 (vectors of all instances ~4 GB)"}
     print(json.dumps(engine_line(args, dets_sigma / elapsed, elapsed, len(insts) * args.steps, stats, extra, clk,
                                  config)), flush=True)
@@ -314,7 +320,7 @@ def run_serve(args):
     jobs = [(t, W.make_job(spec, te)) for t, spec, te in trace]
     t_build = time.perf_counter() - t_build
     max_norb = max(w.norb for _, w in jobs)
-    opts = dict(max_slots=64, max_subspace=12, max_norb=max_norb, max_strings=args.max_strings,
+    opts = dict(max_slots=64, max_subspace=args.engine_subspace, max_norb=max_norb, max_strings=args.max_strings,
                 hbm_budget_bytes=int(args.budget_gb * 1e9))
     small = sorted((w for _, w in jobs), key=lambda w: w.ndets)[:2]
     for _ in range(args.warmup):
@@ -375,7 +381,7 @@ def run_serve(args):
                                 "statuses": {str(k): st64.count(k) for k in sorted(set(st64))}}}
     config = {"workload": f"serve: {n} Poisson arrivals at {args.rate:g}/s, norb in {{24,32,40,48,58}}, "
                           f"nalpha=nbeta=round(norb/3), |A|=|B| log-uniform in [300,{args.max_strings}], own "
-                          f"integrals each; 1 root, mixed sigma, residual <= 1e-3 and Ritz-value change <= 1e-6 Ha; "
+                          f"integrals each; 1 root, mixed sigma, residual <= {jobs[0][1].tol:g} and Ritz-value change <= 1e-6 Ha; "
                           f"admission budget {args.budget_gb:g} GB",
               "step": "the whole trace (arrival of the first job to completion of the last)",
               "l2": "inputs larger than L2"}
@@ -400,6 +406,7 @@ def main():
     ap.add_argument("--rate", type=float, default=20.0, help="arrivals per second of the serve workload")
     ap.add_argument("--max-strings", type=int, default=5000, help="largest |A| = |B| of the serve workload")
     ap.add_argument("--budget-gb", type=float, default=160.0, help="engine admission budget of the serve workload")
+    ap.add_argument("--engine-subspace", type=int, default=20, help="Davidson basis per job in the engine")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -533,7 +540,7 @@ def main():
 
     # sigma-only throughput by precision (sum of the four sigma kernels per vector)
     sigma_rate = {}
-    for p in ("fp64", "mixed"):
+    for p in ("fp64", "mixed", "f32x2"):
         tot = sum(kms[p].values())
         nv = kn[p]["ab_pass"]
         if nv:

@@ -47,6 +47,13 @@ typedef enum {
     SBD_FP64 = 0,  /* FP64 amplitudes, integrals, products and sums */
     SBD_MIXED = 1, /* FP32 amplitudes and integrals, FP32 products and inner
                       sums, FP64 accumulation per output element */
+    SBD_F32X2 = 2, /* FP64 vectors, FP64-accurate arithmetic on the FP32 pipe:
+                      every operand an unevaluated sum of two floats (about
+                      48 significant bits), exact FP32 products with their
+                      rounding errors recovered by fused multiply-adds, two-sum
+                      additions; the same tolerance as SBD_FP64 (1e-12
+                      relative), several times faster on GPUs whose FP64 rate
+                      is a small fraction of their FP32 rate */
 } sbd_precision;
 
 enum {
@@ -84,11 +91,13 @@ typedef struct {
     int timing;              /* nonzero: time every sigma kernel with CUDA events (sbd_kernel_times) */
     double tol_energy;       /* > 0: a root also needs |theta_k - theta_(k-1)| <= tol_energy between
                                 consecutive iterations to count as converged (default 0: off) */
+    int refine_precision;    /* FP64-accurate sigma of the defect corrections of SBD_MIXED solves:
+                                SBD_F32X2 (default) or SBD_FP64 */
 } sbd_options;
 
 typedef struct {
     int iterations;       /* Davidson iterations (all phases) */
-    int sigma_fp64;       /* vectors multiplied by the FP64 sigma */
+    int sigma_fp64;       /* vectors multiplied by an FP64-accurate sigma (SBD_FP64 or SBD_F32X2) */
     int sigma_mixed;      /* vectors multiplied by the mixed sigma */
     int restarts;         /* subspace restarts */
     int refinements;      /* FP64 defect-correction steps (mixed mode) */
@@ -175,8 +184,8 @@ int sbd_lookup(sbd_handle handle, int spin, const uint64_t *keys_dev, int64_t n,
 /*
  * sbd_sigma -- sigma = H c for nvec vectors (paper Sec. II-B Eq. 4; the
  * matrix-free product of Sec. II-A), enqueued on `stream`.
- *   c_dev     device pointer, [nvec][nA][nB], double for SBD_FP64 and float
- *             for SBD_MIXED, in sorted-string order
+ *   c_dev     device pointer, [nvec][nA][nB], double for SBD_FP64 and SBD_F32X2,
+ *             float for SBD_MIXED, in sorted-string order
  *   sigma_dev device pointer, [nvec][nA][nB] doubles (written, not accumulated)
  * The handle keeps one transposed copy of a vector as work space (allocated
  * on the first call).  c and sigma must not overlap.
@@ -189,10 +198,11 @@ int sbd_sigma(sbd_handle handle, const void *c_dev, double *sigma_dev, int nvec,
  * with the damped diagonal preconditioner of Sec. II-E, stopping per
  * Sec. II-G), on the handle's stream.
  *   tol         residual-norm tolerance ||H u - theta u||_2 per root (u normalised)
- *   prec        SBD_FP64, or SBD_MIXED: mixed-precision sigma for the bulk of the
- *               iterations with FP64 defect correction (the converged residual is
- *               always FP64-evaluated); orthogonalisation, the projected
- *               eigenproblem, residuals and energies stay FP64
+ *   prec        SBD_FP64; SBD_F32X2 (every sigma FP64-accurate on the FP32 pipe);
+ *               or SBD_MIXED: mixed-precision sigma for the bulk of the iterations
+ *               with FP64-accurate defect correction (sbd_options.refine_precision;
+ *               the converged residual is always FP64-accurate); orthogonalisation,
+ *               the projected eigenproblem, residuals and energies stay FP64
  *   energies_host  nroots doubles (ascending), ecore included
  *   vecs        NULL, or host or device pointer for [nroots][nA*nB] doubles
  *   residuals_host NULL or nroots doubles
@@ -207,8 +217,9 @@ int sbd_davidson(sbd_handle handle, int nroots, double tol, sbd_precision prec, 
  * the last reset (only when sbd_options.timing was set), measured with CUDA
  * events recorded on the stream each kernel was launched on.  Slots:
  *   0 transpose of C, 1 beta gather pass (rows of C), 2 alpha gather pass
- *   (rows of C^T), 3 alpha-beta pass; FP64 kernels in 0..3, mixed in 4..7.
- * ms_host and launches_host: 8 entries each (either may be NULL).  Waits for
+ *   (rows of C^T), 3 alpha-beta pass; FP64 kernels in 0..3, mixed in 4..7,
+ *   SBD_F32X2 in 8..11.
+ * ms_host and launches_host: 12 entries each (either may be NULL).  Waits for
  * the recorded events; reset != 0 clears the counters afterwards.
  */
 int sbd_kernel_times(sbd_handle handle, double *ms_host, int64_t *launches_host, int reset);

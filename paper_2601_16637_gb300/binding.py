@@ -22,7 +22,9 @@ from . import build as _build
 
 SBD_FP64 = 0
 SBD_MIXED = 1
-PRECISION = {"fp64": SBD_FP64, "mixed": SBD_MIXED, SBD_FP64: SBD_FP64, SBD_MIXED: SBD_MIXED}
+SBD_F32X2 = 2
+PRECISION = {"fp64": SBD_FP64, "mixed": SBD_MIXED, "f32x2": SBD_F32X2, SBD_FP64: SBD_FP64, SBD_MIXED: SBD_MIXED,
+             SBD_F32X2: SBD_F32X2}
 
 STATUS = {
     0: "SBD_OK", 1: "SBD_NOT_CONVERGED", -1: "SBD_ERR_INVALID_ARG", -2: "SBD_ERR_BAD_STRING",
@@ -38,7 +40,7 @@ class sbd_options(C.Structure):
     _fields_ = [("delta", C.c_double), ("max_subspace", C.c_int), ("max_iter", C.c_int),
                 ("hbm_budget_bytes", C.c_size_t), ("ecore", C.c_double), ("table_algo", C.c_int),
                 ("verbose", C.c_int), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("timing", C.c_int), ("tol_energy", C.c_double)]
+                ("timing", C.c_int), ("tol_energy", C.c_double), ("refine_precision", C.c_int)]
 
 
 class sbd_report(C.Structure):
@@ -299,12 +301,12 @@ def sbd_davidson(handle, nroots: int, tol: float, precision, energies: np.ndarra
 
 
 def sbd_kernel_times(handle, reset: bool = False):
-    """({'fp64': {...}, 'mixed': {...}} per-kernel milliseconds, same for launch counts)."""
-    ms = np.zeros(8)
-    n = np.zeros(8, dtype=np.int64)
+    """({'fp64': {...}, 'mixed': {...}, 'f32x2': {...}} per-kernel milliseconds, same for launch counts)."""
+    ms = np.zeros(12)
+    n = np.zeros(12, dtype=np.int64)
     _check(load().sbd_kernel_times(handle, _ptr(ms), _ptr(n), int(bool(reset))), handle)
     out_ms, out_n = {}, {}
-    for p, off in (("fp64", 0), ("mixed", 4)):
+    for p, off in (("fp64", 0), ("mixed", 4), ("f32x2", 8)):
         out_ms[p] = {k: float(ms[off + i]) for i, k in enumerate(KERNEL_SLOTS)}
         out_n[p] = {k: int(n[off + i]) for i, k in enumerate(KERNEL_SLOTS)}
     return out_ms, out_n
@@ -431,7 +433,7 @@ class SBD:
     def __init__(self, norb, nalpha, nbeta, h, eri, A, B, *, stream=None, allocator: str = "torch",
                  delta: float = 1e-4, max_subspace: int = 0, max_iter: int = 200, hbm_budget_bytes: int = 0,
                  ecore: float = 0.0, table_algo: int = 0, verbose: int = 0, timing: bool = False,
-                 tol_energy: float = 0.0):
+                 tol_energy: float = 0.0, refine_precision: str = "f32x2"):
         self._opts = sbd_default_options()
         self._opts.delta = delta
         self._opts.max_subspace = max_subspace
@@ -442,6 +444,7 @@ class SBD:
         self._opts.verbose = verbose
         self._opts.timing = int(bool(timing))
         self._opts.tol_energy = float(tol_energy)
+        self._opts.refine_precision = PRECISION[refine_precision]
         self._alloc = None
         if allocator == "torch":
             self._alloc = _TorchAllocator()
@@ -511,7 +514,7 @@ class SBD:
     def sigma(self, c, precision="fp64", out=None):
         """c: device tensor [N] or [nvec, N] (float64 for fp64, float32 for mixed)."""
         import torch
-        want = torch.float64 if PRECISION[precision] == SBD_FP64 else torch.float32
+        want = torch.float32 if PRECISION[precision] == SBD_MIXED else torch.float64
         if c.dtype != want or not c.is_cuda:
             raise TypeError(f"c must be a CUDA {want} tensor")
         c = c.contiguous()

@@ -146,6 +146,7 @@ void sbd_default_options(sbd_options *opt)
 {
     if (!opt) return;
     memset(opt, 0, sizeof(*opt));
+    opt->refine_precision = SBD_F32X2;
     opt->delta = 1e-4;
     opt->max_subspace = 0;
     opt->max_iter = 200;
@@ -174,7 +175,7 @@ const char *sbd_status_string(int status)
 int sbd_sigma_batched(int n, const sbd_handle *handles, const void *const *c_dev, double *const *sigma_dev,
                       sbd_precision prec, int rows_per_item, void *stream)
 {
-    if (n < 0 || (n > 0 && (!handles || !c_dev || !sigma_dev)) || (prec != SBD_FP64 && prec != SBD_MIXED)) {
+    if (n < 0 || (n > 0 && (!handles || !c_dev || !sigma_dev)) || prec < SBD_FP64 || prec > SBD_F32X2) {
         g_last_error = "sbd_sigma_batched: invalid argument";
         return SBD_ERR_INVALID_ARG;
     }
@@ -197,7 +198,7 @@ int sbd_sigma_batched(int n, const sbd_handle *handles, const void *const *c_dev
         int R = rows_per_item;
         if (R == 0) {
             for (int cand : {4, 2, 1}) {
-                if (cand == 4 && prec == SBD_FP64) continue;
+                if (cand == 4 && prec != SBD_MIXED) continue;
                 if (sigma_batch_smem(prec, cand, max_strings, max_norb) <= sigma_batch_smem_limit(device)) {
                     R = cand;
                     break;
@@ -440,10 +441,10 @@ int sbd_lookup(sbd_handle h, int spin, const uint64_t *keys_dev, int64_t n, int6
 
 int sbd_sigma(sbd_handle h, const void *c_dev, double *sigma_dev, int nvec, sbd_precision prec, void *stream)
 {
-    if (!h || !c_dev || !sigma_dev || nvec < 1 || (prec != SBD_FP64 && prec != SBD_MIXED)) return SBD_ERR_INVALID_ARG;
+    if (!h || !c_dev || !sigma_dev || nvec < 1 || prec < SBD_FP64 || prec > SBD_F32X2) return SBD_ERR_INVALID_ARG;
     return guarded(h, [&]() -> int {
         Ctx &c = h->c;
-        const size_t elem = prec == SBD_FP64 ? sizeof(double) : sizeof(float);
+        const size_t elem = prec == SBD_MIXED ? sizeof(float) : sizeof(double);
         for (int v = 0; v < nvec; ++v)
             sigma_apply(c, static_cast<const char *>(c_dev) + (size_t)v * c.N * elem, sigma_dev + (size_t)v * c.N, prec,
                         (cudaStream_t)stream);
@@ -454,7 +455,7 @@ int sbd_sigma(sbd_handle h, const void *c_dev, double *sigma_dev, int nvec, sbd_
 int sbd_davidson(sbd_handle h, int nroots, double tol, sbd_precision prec, double *energies_host, double *vecs,
                  double *residuals_host, sbd_report *report)
 {
-    if (!h || !energies_host || (prec != SBD_FP64 && prec != SBD_MIXED)) return SBD_ERR_INVALID_ARG;
+    if (!h || !energies_host || prec < SBD_FP64 || prec > SBD_F32X2) return SBD_ERR_INVALID_ARG;
     return guarded(h, [&]() -> int {
         return davidson(h->c, nroots, tol, prec, energies_host, vecs, residuals_host, report);
     });
@@ -465,7 +466,7 @@ int sbd_kernel_times(sbd_handle h, double *ms_host, int64_t *launches_host, int 
     if (!h) return SBD_ERR_INVALID_ARG;
     return guarded(h, [&]() -> int {
         harvest_timing(h->c);
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < 12; ++i) {
             if (ms_host) ms_host[i] = h->c.kernel_ms[i];
             if (launches_host) launches_host[i] = h->c.kernel_n[i];
             if (reset) {

@@ -74,6 +74,8 @@ struct SpinTables {
     double *d_v64_sig = nullptr;
     uint2 *s_pkv32 = nullptr;  // (s_pk_sig, FP32 value bits), for the mixed sigma
     uint2 *d_jv32 = nullptr;   // (d_j_sig, FP32 value bits), for the mixed sigma
+    float2 *s_vx2 = nullptr;   // s_v64_sig as FP32 pairs (hi, lo), for the FP32-pair sigma
+    float2 *d_vx2 = nullptr;   // d_v64_sig as FP32 pairs
     double *ediag = nullptr;     // [n] same-spin diagonal energies
     int max_singles = 0;         // longest singles list
     bool alias = false;          // storage owned by the other spin (A == B)
@@ -103,8 +105,8 @@ struct Ctx {
     };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> event_pool;
-    double kernel_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int64_t kernel_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double kernel_ms[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t kernel_n[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 // the context inside a C-ABI handle (api.cu)

@@ -511,6 +511,9 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
     max_sub = (int)std::min<int64_t>(std::min(max_sub, kMaxSub), N);
     if (max_sub < 2 * nroots && N >= 2 * nroots) max_sub = 2 * nroots;
     const bool mixed = prec == SBD_MIXED;
+    // the FP64-accurate sigma: the solve's own precision, or for mixed solves the refinement precision
+    const sbd_precision exact_prec =
+        mixed ? (c.opt.refine_precision == SBD_F32X2 ? SBD_F32X2 : SBD_FP64) : prec;
 
     // keep the basis inside the budget: V, W, U, HU, corrections (+ FP32 copy)
     auto need = [&](int ms, int nk) {
@@ -570,7 +573,7 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
                     sigma_apply(c, c32, W + b * ld, SBD_MIXED, w.s, V + b * ld);
                     r.sigma_mixed++;
                 } else {
-                    sigma_apply(c, V + b * ld, W + b * ld, SBD_FP64, w.s);
+                    sigma_apply(c, V + b * ld, W + b * ld, exact_prec, w.s);
                     r.sigma_fp64++;
                 }
                 exact[b] = fp64;
@@ -635,7 +638,7 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
             double rmax = *std::max_element(rn.begin(), rn.end());
             if (c.opt.verbose)
                 fprintf(stderr, "[sbd] iter %d k=%d theta0=%.12f rmax=%.3e %s\n", iter, k, th[0] + c.opt.ecore, rmax,
-                        mixed ? "mixed" : "fp64");
+                        mixed ? "mixed" : (prec == SBD_F32X2 ? "f32x2" : "fp64"));
             bool checked = !mixed;
             if (mixed) {
                 hist.push_back(rmax);

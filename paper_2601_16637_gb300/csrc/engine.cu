@@ -669,10 +669,10 @@ void sbd_engine_s::init()
     SBD_CUDA(cudaFuncSetAttribute(e_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(2 * sizeof(double) * kEMaxSub * kEMaxSub)));
     const int ms = std::max(opt.max_strings, 1);
-    // FP64 sigma for the checks: the largest rows per item that fits
+    // FP64-accurate sigma for the checks (FP32 pairs): the largest rows per item that fits
     for (int R : {2, 1})
-        if (sigma_batch_smem(SBD_FP64, R, ms, opt.max_norb) <= sigma_batch_smem_limit(device)) {
-            sb64 = sigma_batch_create(opt.max_slots, SBD_FP64, R, ms, opt.max_norb, device);
+        if (sigma_batch_smem(SBD_F32X2, R, ms, opt.max_norb) <= sigma_batch_smem_limit(device)) {
+            sb64 = sigma_batch_create(opt.max_slots, SBD_F32X2, R, ms, opt.max_norb, device);
             break;
         }
     if (!sb64) fail(SBD_ERR_UNSUPPORTED, "engine: max_strings/max_norb too large for the FP64 sigma staging");

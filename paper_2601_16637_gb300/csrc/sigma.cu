@@ -26,9 +26,15 @@
 // 8-lane group fetches 4 entries with 16-byte loads, and the next column's
 // list bounds are prefetched.  The phase of a single is folded into the
 // shared-memory coefficient tables, which are indexed by 2*code + (phase<0).
-// Precision T = double (FP64) or float (mixed: FP32 amplitudes, integrals,
+// Precision T = double (FP64), float (mixed: FP32 amplitudes, integrals,
 // products and per-list sums, each list sum and the diagonal term accumulated
-// into the FP64 output).
+// into the FP64 output), or F2 (FP64-accurate arithmetic on the FP32 pipe:
+// every amplitude, integral and matrix element is an unevaluated sum hi + lo
+// of two floats, products are exact hi*hi (a fused multiply-add recovers the
+// rounding error, Dekker's product) plus the two cross terms, and sums use
+// Knuth's two-sum; on GB300 the FP32 pipe is ~64x the FP64 pipe).
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace sbd {
@@ -38,8 +44,80 @@ namespace {
 constexpr int kGroup = 8;  // lanes cooperating on one output column
 constexpr int kGroupsPerWarp = 32 / kGroup;
 
+// A value hi + lo of two floats (|lo| <= ulp(hi)/2 after renormalisation).
+struct F2 {
+    float hi, lo;
+    F2() = default;
+    __host__ __device__ constexpr F2(float h) : hi(h), lo(0.f) {}
+    __host__ __device__ constexpr F2(float h, float l) : hi(h), lo(l) {}
+};
+
+__device__ __forceinline__ F2 f2_split(double x)
+{
+    const float hi = __double2float_rn(x);
+    return F2(hi, __double2float_rn(x - (double)hi));
+}
+__device__ __forceinline__ double f2_value(F2 a) { return (double)a.hi + (double)a.lo; }
+
+// acc += a * b.  The product's high part is exact to 48 bits (hi*hi and its rounding error from
+// a fused multiply-add, plus the cross terms); it enters acc.hi through a two-sum whose error
+// joins the low parts, which are gathered in acc.lo and renormalised by f2_add.  The explicit
+// _rn intrinsics keep the compiler from fusing the two-sum into multiply-adds.
+__device__ __forceinline__ void f2_mac(F2 &acc, F2 a, F2 b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float s = __fadd_rn(acc.hi, p);
+    const float bb = __fsub_rn(s, acc.hi);
+    const float t = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, e));
+}
+
+// a + b: two-sum of the high parts, low parts added, renormalised
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    float t = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    t = __fadd_rn(t, __fadd_rn(a.lo, b.lo));
+    const float hi = __fadd_rn(s, t);
+    return F2(hi, __fsub_rn(t, __fsub_rn(hi, s)));
+}
+
+template <typename T>
+constexpr bool kIsF2 = std::is_same<T, F2>::value;
+
+// element type of the vectors a pass reads (the pair precision reads FP64 vectors)
+template <typename T>
+struct In {
+    using type = T;
+};
+template <>
+struct In<F2> {
+    using type = double;
+};
+
+template <typename T>
+__device__ __forceinline__ T conv(double x)
+{
+    if constexpr (kIsF2<T>) return f2_split(x);
+    else return (T)x;
+}
+template <typename T>
+__device__ __forceinline__ T conv(float x)
+{
+    return (T)x;
+}
+
 template <typename T>
 struct Threads;
+template <>
+struct Threads<F2> {
+    static constexpr int value = 512;
+};
 template <>
 struct Threads<float> {
     static constexpr int value = 1024;
@@ -91,6 +169,28 @@ struct VecIO<double, 2> {
     {
         *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
     }
+};
+template <>
+struct VecIO<F2, 2> {
+    __device__ static void ld(const F2 *p, F2 (&v)[2])
+    {
+        const float4 x = *reinterpret_cast<const float4 *>(p);
+        v[0] = F2(x.x, x.y);
+        v[1] = F2(x.z, x.w);
+    }
+    __device__ static void st(F2 *p, const F2 (&v)[2])
+    {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
+    }
+};
+template <>
+struct VecIO<F2, 1> {
+    __device__ static void ld(const F2 *p, F2 (&v)[1])
+    {
+        const float2 x = *reinterpret_cast<const float2 *>(p);
+        v[0] = F2(x.x, x.y);
+    }
+    __device__ static void st(F2 *p, const F2 (&v)[1]) { *reinterpret_cast<float2 *>(p) = make_float2(v[0].hi, v[0].lo); }
 };
 template <typename T>
 struct VecIO<T, 1> {
@@ -163,9 +263,33 @@ struct Lists<double> {
     }
 };
 
+template <>
+struct Lists<F2> {
+    const uint32_t *spk;
+    const float2 *sv;
+    const int32_t *dj;
+    const float2 *dv;
+    __device__ void singles4(int64_t e, uint32_t (&pk)[4], F2 (&v)[4]) const
+    {
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(spk + e));
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(sv + e));
+        const float4 c = __ldg(reinterpret_cast<const float4 *>(sv + e + 2));
+        pk[0] = a.x, pk[1] = a.y, pk[2] = a.z, pk[3] = a.w;
+        v[0] = F2(b.x, b.y), v[1] = F2(b.z, b.w), v[2] = F2(c.x, c.y), v[3] = F2(c.z, c.w);
+    }
+    __device__ void doubles4(int64_t e, int (&j)[4], F2 (&v)[4]) const
+    {
+        const int4 a = __ldg(reinterpret_cast<const int4 *>(dj + e));
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(dv + e));
+        const float4 c = __ldg(reinterpret_cast<const float4 *>(dv + e + 2));
+        j[0] = a.x, j[1] = a.y, j[2] = a.z, j[3] = a.w;
+        v[0] = F2(b.x, b.y), v[1] = F2(b.z, b.w), v[2] = F2(c.x, c.y), v[3] = F2(c.z, c.w);
+    }
+};
+
 template <typename T>
 struct RowArgs {
-    const T *X;  // [nrow][ncol]
+    const typename In<T>::type *X;  // [nrow][ncol]
     int64_t nrow, ncol;
     double *Y;  // output element (row r, column c) at r*y_rs + c*y_cs
     int64_t y_rs, y_cs;
@@ -202,7 +326,7 @@ __device__ __forceinline__ void row_group(const RowArgs<T> &a, int64_t r0, unsig
             for (int64_t c = tid; c < a.ncol; c += kThreads) {
                 T v[R];
 #pragma unroll
-                for (int r = 0; r < R; ++r) v[r] = r < nr ? a.X[(r0 + r) * a.ncol + c] : T(0);
+                for (int r = 0; r < R; ++r) v[r] = r < nr ? conv<T>(a.X[(r0 + r) * a.ncol + c]) : T(0);
                 VecIO<T, R>::st(Xs + c * R, v);
             }
         }
@@ -219,7 +343,7 @@ __device__ __forceinline__ void row_group(const RowArgs<T> &a, int64_t r0, unsig
                         const int k = __ffsll((long long)m) - 1;
                         s += __ldg(a.eri + (size_t)code * n2 + (size_t)k * (a.norb + 1));
                     }
-                v[r] = (T)((key & 1) ? -s : s);
+                v[r] = conv<T>((key & 1) ? -s : s);
             }
             VecIO<T, R>::st(Js + (size_t)key * R, v);
         }
@@ -256,10 +380,17 @@ __device__ __forceinline__ void row_group(const RowArgs<T> &a, int64_t r0, unsig
                     for (int u = 0; u < 4; ++u) {
                         T xj[R], jv[R];
                         if (STAGED) VecIO<T, R>::ld(Xs + (size_t)pk_j(pk[u]) * R, xj);
-                        else xj[0] = a.X[r0 * a.ncol + pk_j(pk[u])];
+                        else xj[0] = conv<T>(a.X[r0 * a.ncol + pk_j(pk[u])]);
                         VecIO<T, R>::ld(Js + (size_t)pk_key(pk[u]) * R, jv);
 #pragma unroll
-                        for (int r = 0; r < R; ++r) acc[r] += (v[u] + jv[r]) * xj[r];
+                        for (int r = 0; r < R; ++r) {
+                            if constexpr (kIsF2<T>) {
+                                f2_mac(acc[r], v[u], xj[r]);
+                                f2_mac(acc[r], jv[r], xj[r]);
+                            } else {
+                                acc[r] += (v[u] + jv[r]) * xj[r];
+                            }
+                        }
                     }
                 }
                 for (int i = kListPad * lig; i < ld; i += kGroup * kListPad) {
@@ -270,22 +401,37 @@ __device__ __forceinline__ void row_group(const RowArgs<T> &a, int64_t r0, unsig
                     for (int u = 0; u < 4; ++u) {
                         T xj[R];
                         if (STAGED) VecIO<T, R>::ld(Xs + (size_t)jj[u] * R, xj);
-                        else xj[0] = a.X[r0 * a.ncol + jj[u]];
+                        else xj[0] = conv<T>(a.X[r0 * a.ncol + jj[u]]);
 #pragma unroll
-                        for (int r = 0; r < R; ++r) acc[r] += v[u] * xj[r];
+                        for (int r = 0; r < R; ++r) {
+                            if constexpr (kIsF2<T>) f2_mac(acc[r], v[u], xj[r]);
+                            else acc[r] += v[u] * xj[r];
+                        }
                     }
                 }
             }
 #pragma unroll
             for (int off = kGroup / 2; off > 0; off >>= 1)
 #pragma unroll
-                for (int r = 0; r < R; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], off, kGroup);
+                for (int r = 0; r < R; ++r) {
+                    if constexpr (kIsF2<T>) {
+                        const F2 o(__shfl_xor_sync(0xffffffffu, acc[r].hi, off, kGroup),
+                                   __shfl_xor_sync(0xffffffffu, acc[r].lo, off, kGroup));
+                        acc[r] = f2_add(acc[r], o);
+                    } else {
+                        acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], off, kGroup);
+                    }
+                }
             if (valid && lig < nr) {
-                double out = (double)pick<R>(acc, lig);
+                double out;
+                if constexpr (kIsF2<T>) out = f2_value(pick<R>(acc, lig));
+                else out = (double)pick<R>(acc, lig);
                 const int64_t idx = (r0 + lig) * a.y_rs + c * a.y_cs;
                 if (a.hd) {
-                    const double xc = a.xd64 ? a.xd64[(r0 + lig) * a.ncol + c]
-                                             : (double)(STAGED ? Xs[(size_t)c * R + lig] : a.X[(r0 + lig) * a.ncol + c]);
+                    double xc;
+                    if constexpr (kIsF2<T>) xc = a.X[(r0 + lig) * a.ncol + c];  // the FP64 input itself
+                    else xc = a.xd64 ? a.xd64[(r0 + lig) * a.ncol + c]
+                                     : (double)(STAGED ? Xs[(size_t)c * R + lig] : a.X[(r0 + lig) * a.ncol + c]);
                     out += a.hd[idx] * xc;
                 }
                 a.Y[idx] = a.accumulate ? a.Y[idx] + out : out;
@@ -303,11 +449,11 @@ __global__ void __launch_bounds__(Threads<T>::value) row_pass_kernel(const RowAr
 
 template <typename T>
 struct AbArgs {
-    const T *C;  // [nA][nB]
-    double *S;   // [nA][nB], accumulated
+    const typename In<T>::type *C;  // [nA][nB]
+    double *S;                       // [nA][nB], accumulated
     int64_t nA, nB;
     int norb;
-    const T *eri;  // (pq|rs) as a [norb^2][norb^2] matrix
+    const typename In<T>::type *eri;  // (pq|rs) as a [norb^2][norb^2] matrix
     const int64_t *as_ptr;
     const uint32_t *as_pk;
     const int64_t *bs_ptr;
@@ -352,17 +498,24 @@ __device__ __forceinline__ void ab_row(const AbArgs<T> &a, int64_t ia, unsigned 
                 for (int64_t c = tid; c < a.nB; c += kThreads) {
                     T v[R];
 #pragma unroll
-                    for (int k = 0; k < R; ++k) v[k] = k < kr ? a.C[ja[k] * a.nB + c] : T(0);
+                    for (int k = 0; k < R; ++k) v[k] = k < kr ? conv<T>(a.C[ja[k] * a.nB + c]) : T(0);
                     VecIO<T, R>::st(Cs + c * R, v);
                 }
             }
             // sign-folded W: row key = 2*rs + t holds (t ? -1 : 1) * u_k (p_k q_k|rs); rs = 0 rows zero
             for (int key = tid; key < 2 * n2; key += kThreads) {
                 const int code = key >> 1;
-                const T sg = (key & 1) ? T(-1) : T(1);
                 T v[R];
+                if constexpr (kIsF2<T>) {
+                    const double sg = (key & 1) ? -1.0 : 1.0;
 #pragma unroll
-                for (int k = 0; k < R; ++k) v[k] = code ? sg * u[k] * __ldg(a.eri + (size_t)pq[k] * n2 + code) : T(0);
+                    for (int k = 0; k < R; ++k)
+                        v[k] = code ? f2_split(sg * (double)u[k].hi * __ldg(a.eri + (size_t)pq[k] * n2 + code)) : T(0);
+                } else {
+                    const T sg = (key & 1) ? T(-1) : T(1);
+#pragma unroll
+                    for (int k = 0; k < R; ++k) v[k] = code ? sg * u[k] * __ldg(a.eri + (size_t)pq[k] * n2 + code) : T(0);
+                }
                 VecIO<T, R>::st(Ws + (size_t)key * R, v);
             }
             __syncthreads();
@@ -392,9 +545,12 @@ __device__ __forceinline__ void ab_row(const AbArgs<T> &a, int64_t ia, unsigned 
                         for (int t = 0; t < 4; ++t) {
                             T cv[R], wv[R];
                             if (STAGED) VecIO<T, R>::ld(Cs + (size_t)pk_j(pk[t]) * R, cv);
-                            else cv[0] = a.C[ja[0] * a.nB + pk_j(pk[t])];
+                            else cv[0] = conv<T>(a.C[ja[0] * a.nB + pk_j(pk[t])]);
                             VecIO<T, R>::ld(Ws + (size_t)pk_key(pk[t]) * R, wv);
-                            if constexpr (sizeof(T) == 4) {
+                            if constexpr (kIsF2<T>) {
+#pragma unroll
+                                for (int k = 0; k < R; ++k) f2_mac(acc, wv[k], cv[k]);
+                            } else if constexpr (sizeof(T) == 4) {
                                 // FP32: one short chain per entry keeps the four entries independent
                                 part[t] = wv[0] * cv[0];
 #pragma unroll
@@ -408,9 +564,21 @@ __device__ __forceinline__ void ab_row(const AbArgs<T> &a, int64_t ia, unsigned 
                         if constexpr (sizeof(T) == 4) acc += (part[0] + part[1]) + (part[2] + part[3]);
                     }
                 }
+                double total;
+                if constexpr (kIsF2<T>) {
 #pragma unroll
-                for (int off = kGroup / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off, kGroup);
-                if (valid && lig == 0) atomicAdd(a.S + ia * a.nB + ib, (double)acc);
+                    for (int off = kGroup / 2; off > 0; off >>= 1) {
+                        const F2 o(__shfl_xor_sync(0xffffffffu, acc.hi, off, kGroup),
+                                   __shfl_xor_sync(0xffffffffu, acc.lo, off, kGroup));
+                        acc = f2_add(acc, o);
+                    }
+                    total = f2_value(acc);
+                } else {
+#pragma unroll
+                    for (int off = kGroup / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off, kGroup);
+                    total = (double)acc;
+                }
+                if (valid && lig == 0) atomicAdd(a.S + ia * a.nB + ib, total);
             }
         }
     }
@@ -528,6 +696,17 @@ Lists<double> lists_of<double>(const SpinTables &t)
 {
     return Lists<double>{t.s_pk_sig, t.s_v64_sig, t.d_j_sig, t.d_v64_sig};
 }
+template <>
+Lists<F2> lists_of<F2>(const SpinTables &t)
+{
+    return Lists<F2>{t.s_pk_sig, t.s_vx2, t.d_j_sig, t.d_vx2};
+}
+
+// timing slot of the first sigma kernel of a precision (transpose, beta, alpha, alpha-beta follow)
+template <typename T>
+constexpr int kSlotBase = kIsF2<T> ? 8 : (sizeof(T) == 4 ? 4 : 0);
+template <typename T>
+constexpr int kRowsMax = sizeof(T) == 4 ? 4 : 2;
 
 // Runs launch(); when timing is on, brackets it with events on stream s and
 // queues the pair for sbd_kernel_times (slot: kernel kind, +4 for FP32).
@@ -548,8 +727,8 @@ void timed(Ctx &c, int slot, cudaStream_t s, F &&launch)
 // Arguments of the three gather passes of one instance: beta pass on C, alpha pass on its
 // transpose Ct, alpha-beta pass on C (the single-instance and the batched launches share them).
 template <typename T>
-void make_args(const Ctx &c, const T *C, double *S, const double *c64, const T *Ct, RowArgs<T> &rb, RowArgs<T> &ra,
-               AbArgs<T> &ab)
+void make_args(const Ctx &c, const typename In<T>::type *C, double *S, const double *c64,
+               const typename In<T>::type *Ct, RowArgs<T> &rb, RowArgs<T> &ra, AbArgs<T> &ab)
 {
     const SpinTables &ta = c.sp[0], &tb = c.sp[1];
     rb = RowArgs<T>{};
@@ -589,7 +768,8 @@ void make_args(const Ctx &c, const T *C, double *S, const double *c64, const T *
     ab.nA = c.nA;
     ab.nB = c.nB;
     ab.norb = c.norb;
-    ab.eri = sizeof(T) == 4 ? (const T *)(const void *)c.eri32 : (const T *)(const void *)c.eri64;
+    using E = typename In<T>::type;
+    ab.eri = sizeof(E) == 4 ? (const E *)(const void *)c.eri32 : (const E *)(const void *)c.eri64;
     ab.as_ptr = ta.s_ptr;      // canonical alpha lists: exact counts for the row groups
     ab.as_pk = ta.s_pk;
     ab.bs_ptr = tb.sig_s_ptr;  // padded beta lists for 16-byte loads
@@ -597,14 +777,15 @@ void make_args(const Ctx &c, const T *C, double *S, const double *c64, const T *
 }
 
 template <typename T>
-void apply(Ctx &c, const T *C, double *S, const double *c64, cudaStream_t s)
+void apply(Ctx &c, const typename In<T>::type *C, double *S, const double *c64, cudaStream_t s)
 {
+    using E = typename In<T>::type;
     const int n2 = c.norb * c.norb;
-    const int rmax = sizeof(T) == 4 ? 4 : 2;
+    const int rmax = kRowsMax<T>;
     const size_t lim = smem_limit(c);
-    const int base = sizeof(T) == 4 ? 4 : 0;
-    T *Ct = static_cast<T *>(c.work_t);
-    timed(c, base + 0, s, [&] { transpose<T>(C, Ct, c.nA, c.nB, s); });
+    const int base = kSlotBase<T>;
+    E *Ct = static_cast<E *>(c.work_t);
+    timed(c, base + 0, s, [&] { transpose<E>(C, Ct, c.nA, c.nB, s); });
     RowArgs<T> rb, ra;
     AbArgs<T> ab;
     make_args<T>(c, C, S, c64, Ct, rb, ra, ab);
@@ -645,7 +826,7 @@ Layout layout_for(int m)
     L.off_b = take(sizeof(int64_t) * (m + 1));
     L.off_a = take(sizeof(int64_t) * (m + 1));
     L.off_ab = take(sizeof(int64_t) * (m + 1));
-    L.td = take(sizeof(TDesc<T>) * m);
+    L.td = take(sizeof(TDesc<typename In<T>::type>) * m);
     L.rb = take(sizeof(RowArgs<T>) * m);
     L.ra = take(sizeof(RowArgs<T>) * m);
     L.ab = take(sizeof(AbArgs<T>) * m);
@@ -768,17 +949,18 @@ void batch_set(SigmaBatch *b, const SigmaSlot *slots, int n)
     *reinterpret_cast<int *>(h + L.n) = n;
     int64_t *ot = reinterpret_cast<int64_t *>(h + L.off_t), *ob = reinterpret_cast<int64_t *>(h + L.off_b);
     int64_t *oa = reinterpret_cast<int64_t *>(h + L.off_a), *oab = reinterpret_cast<int64_t *>(h + L.off_ab);
-    TDesc<T> *td = reinterpret_cast<TDesc<T> *>(h + L.td);
+    using E = typename In<T>::type;
+    TDesc<E> *td = reinterpret_cast<TDesc<E> *>(h + L.td);
     RowArgs<T> *rb = reinterpret_cast<RowArgs<T> *>(h + L.rb), *ra = reinterpret_cast<RowArgs<T> *>(h + L.ra);
     AbArgs<T> *ab = reinterpret_cast<AbArgs<T> *>(h + L.ab);
     ot[0] = ob[0] = oa[0] = oab[0] = 0;
     for (int i = 0; i < n; ++i) {
         const SigmaSlot &sl = slots[i];
         const Ctx &c = *sl.c;
-        const T *x = static_cast<const T *>(sl.x);
-        T *xt = static_cast<T *>(sl.xt);
+        const E *x = static_cast<const E *>(sl.x);
+        E *xt = static_cast<E *>(sl.xt);
         make_args<T>(c, x, sl.y, sl.x64, xt, rb[i], ra[i], ab[i]);
-        td[i] = TDesc<T>{x, xt, c.nA, c.nB};
+        td[i] = TDesc<E>{x, xt, c.nA, c.nB};
         ot[i + 1] = ot[i] + ((c.nA + 31) / 32) * ((c.nB + 31) / 32);
         ob[i + 1] = ob[i] + (c.nA + b->R - 1) / b->R;
         oa[i + 1] = oa[i] + (c.nB + b->R - 1) / b->R;
@@ -793,8 +975,9 @@ void batch_launch_r(SigmaBatch *b, cudaStream_t s)
     const Layout &L = b->L;
     unsigned char *d = b->dev;
     const int *pn = reinterpret_cast<const int *>(d + L.n);
-    transpose_batch_kernel<T><<<b->grid_t, dim3(32, 8), 0, s>>>(pn, reinterpret_cast<const int64_t *>(d + L.off_t),
-                                                                reinterpret_cast<const TDesc<T> *>(d + L.td));
+    using E = typename In<T>::type;
+    transpose_batch_kernel<E><<<b->grid_t, dim3(32, 8), 0, s>>>(pn, reinterpret_cast<const int64_t *>(d + L.off_t),
+                                                                reinterpret_cast<const TDesc<E> *>(d + L.td));
     SBD_LAUNCH("transpose_batch_kernel");
     row_batch_kernel<T, R><<<b->grid_pass, kThreads, b->smem, s>>>(
         pn, reinterpret_cast<const int64_t *>(d + L.off_b), reinterpret_cast<const RowArgs<T> *>(d + L.rb), b->counters);
@@ -831,11 +1014,12 @@ void sigma_prepare(Ctx &c)
 {
     set_attrs<double>(c.smem_optin);
     set_attrs<float>(c.smem_optin);
+    set_attrs<F2>(c.smem_optin);
 }
 
 size_t sigma_batch_smem(sbd_precision prec, int R, int max_strings, int max_norb)
 {
-    return batch_smem(prec == SBD_FP64 ? 8 : 4, R, max_strings, max_norb);
+    return batch_smem(prec == SBD_MIXED ? 4 : 8, R, max_strings, max_norb);
 }
 
 size_t sigma_batch_smem_limit(int device)
@@ -848,7 +1032,7 @@ size_t sigma_batch_smem_limit(int device)
 SigmaBatch *sigma_batch_create(int max_slots, sbd_precision prec, int R, int max_strings, int max_norb, int device)
 {
     if (max_slots < 1) fail(SBD_ERR_INVALID_ARG, "batched sigma needs at least one slot");
-    if (!(R == 1 || R == 2 || (R == 4 && prec == SBD_MIXED)))
+    if (!(R == 1 || R == 2 || (R == 4 && prec == SBD_MIXED)) || prec < SBD_FP64 || prec > SBD_F32X2)
         fail(SBD_ERR_INVALID_ARG, "rows per work item must be 1, 2 or (mixed only) 4");
     const size_t smem = sigma_batch_smem(prec, R, max_strings, max_norb);
     if (smem > sigma_batch_smem_limit(device))
@@ -859,7 +1043,8 @@ SigmaBatch *sigma_batch_create(int max_slots, sbd_precision prec, int R, int max
     b->R = R;
     b->device = device;
     b->smem = smem;
-    b->L = prec == SBD_FP64 ? layout_for<double>(max_slots) : layout_for<float>(max_slots);
+    b->L = prec == SBD_FP64 ? layout_for<double>(max_slots)
+                            : (prec == SBD_F32X2 ? layout_for<F2>(max_slots) : layout_for<float>(max_slots));
     try {
         SBD_CUDA(cudaMalloc(&b->dev, b->L.total));
         SBD_CUDA(cudaMallocHost(&b->host, b->L.total));
@@ -868,6 +1053,9 @@ SigmaBatch *sigma_batch_create(int max_slots, sbd_precision prec, int R, int max
         if (prec == SBD_FP64) {
             if (R == 2) batch_attrs<double, 2>(b);
             else batch_attrs<double, 1>(b);
+        } else if (prec == SBD_F32X2) {
+            if (R == 2) batch_attrs<F2, 2>(b);
+            else batch_attrs<F2, 1>(b);
         } else {
             if (R == 4) batch_attrs<float, 4>(b);
             else if (R == 2) batch_attrs<float, 2>(b);
@@ -891,6 +1079,7 @@ void sigma_batch_set(SigmaBatch *b, const SigmaSlot *slots, int n)
             fail(SBD_ERR_UNSUPPORTED, "batched sigma: an instance exceeds the string or orbital limit of the batch");
     }
     if (b->prec == SBD_FP64) batch_set<double>(b, slots, n);
+    else if (b->prec == SBD_F32X2) batch_set<F2>(b, slots, n);
     else batch_set<float>(b, slots, n);
 }
 
@@ -901,6 +1090,9 @@ void sigma_batch_launch(SigmaBatch *b, cudaStream_t s)
     if (b->prec == SBD_FP64) {
         if (b->R == 2) batch_launch_r<double, 2>(b, s);
         else batch_launch_r<double, 1>(b, s);
+    } else if (b->prec == SBD_F32X2) {
+        if (b->R == 2) batch_launch_r<F2, 2>(b, s);
+        else batch_launch_r<F2, 1>(b, s);
     } else {
         if (b->R == 4) batch_launch_r<float, 4>(b, s);
         else if (b->R == 2) batch_launch_r<float, 2>(b, s);
@@ -922,6 +1114,7 @@ void sigma_batch_destroy(SigmaBatch *b)
 void sigma_apply(Ctx &c, const void *cvec, double *svec, sbd_precision prec, cudaStream_t s, const double *c64)
 {
     if (prec == SBD_FP64) apply<double>(c, static_cast<const double *>(cvec), svec, nullptr, s);
+    else if (prec == SBD_F32X2) apply<F2>(c, static_cast<const double *>(cvec), svec, nullptr, s);
     else apply<float>(c, static_cast<const float *>(cvec), svec, c64, s);
 }
 

@@ -410,6 +410,16 @@ __global__ void pair_kernel(const uint32_t *__restrict__ key, const double *__re
         out[i] = make_uint2(key[i], __float_as_uint(__double2float_rn(val[i])));
 }
 
+// x = hi + lo with hi the FP32 rounding of x and lo the FP32 rounding of the remainder
+__global__ void split_kernel(const double *__restrict__ in, float2 *out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = in[i];
+        const float hi = __double2float_rn(x);
+        out[i] = make_float2(hi, __double2float_rn(x - (double)hi));
+    }
+}
+
 __global__ void to_float_kernel(const double *in, float *out, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -552,6 +562,8 @@ void build_tables(Ctx &c, int spin)
     t.d_j_sig = dalloc_n<int32_t>(c, t.sig_nd);
     t.d_v64_sig = dalloc_n<double>(c, t.sig_nd);
     t.d_jv32 = dalloc_n<uint2>(c, t.sig_nd);
+    t.s_vx2 = dalloc_n<float2>(c, t.sig_ns);
+    t.d_vx2 = dalloc_n<float2>(c, t.sig_nd);
     int64_t *perm = dalloc_n<int64_t>(c, (size_t)std::max<int64_t>(std::max(t.sig_ns, t.sig_nd), 1));
     const int ob = blocks_for(n, 128);
     if (t.sig_ns) {
@@ -563,6 +575,8 @@ void build_tables(Ctx &c, int spin)
         SBD_LAUNCH("gather_kernel(singles)");
         pair_kernel<<<gb, 256, 0, c.stream>>>(t.s_pk_sig, t.s_v64_sig, t.s_pkv32, t.sig_ns);
         SBD_LAUNCH("pair_kernel(singles)");
+        split_kernel<<<gb, 256, 0, c.stream>>>(t.s_v64_sig, t.s_vx2, t.sig_ns);
+        SBD_LAUNCH("split_kernel(singles)");
     }
     if (t.sig_nd) {
         sigma_order_kernel<<<ob, 128, 0, c.stream>>>(t.d_ptr, t.sig_d_ptr, n, t.d_j, perm);
@@ -574,6 +588,8 @@ void build_tables(Ctx &c, int spin)
         pair_kernel<<<gb, 256, 0, c.stream>>>(reinterpret_cast<const uint32_t *>(t.d_j_sig), t.d_v64_sig, t.d_jv32,
                                                t.sig_nd);
         SBD_LAUNCH("pair_kernel(doubles)");
+        split_kernel<<<gb, 256, 0, c.stream>>>(t.d_v64_sig, t.d_vx2, t.sig_nd);
+        SBD_LAUNCH("split_kernel(doubles)");
     }
     dfree(c, perm);
     t.ediag = dalloc_n<double>(c, n);

@@ -17,7 +17,7 @@ import numpy as np
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="cfg3-6000")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "f32x2"])
     ap.add_argument("--reps", type=int, default=2)
     args = ap.parse_args()
 

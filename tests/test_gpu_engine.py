@@ -55,7 +55,7 @@ def _vectors(torch, gs, dtype, seed):
     return [torch.from_numpy(W.random_vector(g.N, seed + i)[0]).to("cuda", dtype) for i, g in enumerate(gs)]
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("prec", ["mixed", "fp64", "f32x2"])
 def test_sigma_batched_is_bitwise_the_single_instance_sigma(torch, B, handles, prec):
     insts, gs = handles
     dt = torch.float32 if prec == "mixed" else torch.float64
@@ -70,7 +70,7 @@ def test_sigma_batched_is_bitwise_the_single_instance_sigma(torch, B, handles, p
     outs1 = [torch.empty(g.N, dtype=torch.float64, device="cuda") for g in gs]
     B.sbd_sigma_batched([g.handle for g in gs], xs, outs1, prec, rows_per_item=1)
     for r, o in zip(ref, outs1):
-        assert rel_maxnorm(o.cpu().numpy(), r.cpu().numpy()) < (2e-6 if prec == "mixed" else 1e-14)
+        assert rel_maxnorm(o.cpu().numpy(), r.cpu().numpy()) < {"mixed": 2e-6, "fp64": 1e-14, "f32x2": 1e-13}[prec]
 
 
 def test_sigma_batched_fp64_matches_the_oracle(torch, B, handles, oracle_mod):

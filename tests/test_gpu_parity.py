@@ -147,10 +147,11 @@ def test_diagonal_against_oracle(torch, B, med_pair):
 # sigma
 
 
-def test_sigma_fp64_full_against_oracle(torch, B, med_pair):
+@pytest.mark.parametrize("prec", ["fp64", "f32x2"])
+def test_sigma_fp64_full_against_oracle(torch, B, med_pair, prec):
     wl, g, o = med_pair
     x = W.random_vector(g.N, 7, nvec=2)
-    got = g.sigma(torch.from_numpy(x).cuda(), "fp64").cpu().numpy()
+    got = g.sigma(torch.from_numpy(x).cuda(), prec).cpu().numpy()
     ref = o.sigma(x)
     assert rel_maxnorm(got, ref) <= SIGMA_FP64_RTOL
 
@@ -160,8 +161,10 @@ def test_sigma_fp64_unequal_electrons_and_sets(torch, B, oracle_mod):
     with B.SBD.from_workload(wl) as g:
         o = oracle_mod.Oracle.from_workload(wl)
         x = W.random_vector(g.N, 8)
-        got = g.sigma(torch.from_numpy(x[0]).cuda(), "fp64").cpu().numpy()
-        assert rel_maxnorm(got, o.sigma(x)[0]) <= SIGMA_FP64_RTOL
+        ref = o.sigma(x)[0]
+        for prec in ("fp64", "f32x2"):
+            got = g.sigma(torch.from_numpy(x[0]).cuda(), prec).cpu().numpy()
+            assert rel_maxnorm(got, ref) <= SIGMA_FP64_RTOL, prec
 
 
 def test_sigma_mixed_against_fp64(torch, B, med_pair):
@@ -203,6 +206,10 @@ def test_sigma_cfg2_full_size_sampled_rows(torch, B, cfg2_pair):
     rows = np.random.default_rng(5).integers(0, g.N, 400)
     ref = o.sigma_rows(x, rows)[0]
     assert rel_maxnorm(got[rows], ref) <= SIGMA_FP64_RTOL
+    # the FP32-pair sigma against the FP64 one on every element, and against the oracle rows
+    got2 = g.sigma(torch.from_numpy(x).cuda(), "f32x2").cpu().numpy()
+    assert rel_maxnorm(got2, got) <= 1e-13
+    assert rel_maxnorm(got2[rows], ref) <= SIGMA_FP64_RTOL
 
 
 @pytest.mark.parametrize("shape", [(1, 40), (37, 1), (1, 1)])
@@ -212,8 +219,9 @@ def test_sigma_degenerate_single_string_sets(torch, B, oracle_mod, shape):
     with B.SBD.from_workload(wl) as g:
         o = oracle_mod.Oracle.from_workload(wl)
         x = W.random_vector(g.N, 1)
-        got = g.sigma(torch.from_numpy(x[0]).cuda(), "fp64").cpu().numpy()
-        assert rel_maxnorm(got, o.sigma(x)[0]) <= SIGMA_FP64_RTOL
+        for prec in ("fp64", "f32x2"):
+            got = g.sigma(torch.from_numpy(x[0]).cuda(), prec).cpu().numpy()
+            assert rel_maxnorm(got, o.sigma(x)[0]) <= SIGMA_FP64_RTOL, prec
 
 
 def test_sigma_zero_and_full_shells(torch, B, oracle_mod):
@@ -226,8 +234,9 @@ def test_sigma_zero_and_full_shells(torch, B, oracle_mod):
         with B.SBD(norb, na, nb, h, eri, A, Bs) as g:
             o = oracle_mod.Oracle(norb, na, nb, h, eri, A, Bs)
             x = W.random_vector(g.N, 2)
-            got = g.sigma(torch.from_numpy(x[0]).cuda(), "fp64").cpu().numpy()
-            assert rel_maxnorm(got, o.sigma(x)[0]) <= SIGMA_FP64_RTOL
+            for prec in ("fp64", "f32x2"):
+                got = g.sigma(torch.from_numpy(x[0]).cuda(), prec).cpu().numpy()
+                assert rel_maxnorm(got, o.sigma(x)[0]) <= SIGMA_FP64_RTOL, prec
 
 
 def test_sigma_norb_64(torch, B, oracle_mod):
@@ -252,8 +261,9 @@ def test_sigma_norb_64(torch, B, oracle_mod):
                 for x, y in zip(got, ref):
                     assert np.array_equal(x, y)
         x = W.random_vector(g.N, 3)
-        got = g.sigma(torch.from_numpy(x[0]).cuda(), "fp64").cpu().numpy()
-        assert rel_maxnorm(got, o.sigma(x)[0]) <= SIGMA_FP64_RTOL
+        for prec in ("fp64", "f32x2"):
+            got = g.sigma(torch.from_numpy(x[0]).cuda(), prec).cpu().numpy()
+            assert rel_maxnorm(got, o.sigma(x)[0]) <= SIGMA_FP64_RTOL, prec
 
 
 # ---------------------------------------------------------------------------
@@ -288,10 +298,11 @@ def med_lanczos(med_pair):
     return ev[order], vec[:, order].T
 
 
-def test_davidson_three_roots_against_lanczos(torch, B, med_pair, med_lanczos):
+@pytest.mark.parametrize("prec", ["fp64", "f32x2"])
+def test_davidson_three_roots_against_lanczos(torch, B, med_pair, med_lanczos, prec):
     wl, g, o = med_pair
     e_ref, v_ref = med_lanczos
-    res = g.davidson(nroots=3, tol=1e-8)
+    res = g.davidson(nroots=3, tol=1e-8, precision=prec)
     assert res.status == 0
     assert np.abs(res.energies - e_ref).max() <= EIG_FP64_ATOL
     V = res.vectors.cpu().numpy()
@@ -314,6 +325,10 @@ def test_davidson_mixed_matches_fp64(torch, B, med_pair, med_lanczos):
     assert rmx.residuals[0] <= 1e-7
     # the mixed solve needs at most a few FP64 sigma products
     assert rmx.report["sigma_fp64"] <= 10
+    # defect corrections with the IEEE FP64 sigma instead of FP32 pairs
+    with B.SBD.from_workload(wl, refine_precision="fp64") as g64:
+        r2 = g64.davidson(nroots=1, tol=1e-7, precision="mixed")
+        assert r2.status == 0 and abs(r2.energies[0] - r64.energies[0]) <= EIG_MIXED_ATOL
 
 
 def test_davidson_mixed_three_roots(torch, B, med_pair, med_lanczos):
@@ -424,6 +439,9 @@ def test_sigma_cfg3_full_size_sampled_rows(torch, B, cfg3_pair):
     ref = o.sigma_rows(x, rows)[0]
     s64 = g.sigma(xt, "fp64").cpu().numpy()
     assert rel_maxnorm(s64[rows], ref) <= SIGMA_FP64_RTOL
+    s2 = g.sigma(xt, "f32x2").cpu().numpy()
+    assert rel_maxnorm(s2[rows], ref) <= SIGMA_FP64_RTOL
+    assert rel_maxnorm(s2, s64) <= 1e-13
     s32 = g.sigma(xt.float(), "mixed").cpu().numpy()
     assert rel_maxnorm(s32[rows], ref) <= SIGMA_MIXED_RTOL
 
