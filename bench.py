@@ -251,7 +251,7 @@ def run_batch(args):
 
     B.load(build_if_missing=True)
     insts = W.batch_instances(args.batch_n)
-    opts = dict(max_slots=len(insts), max_subspace=args.engine_subspace, max_norb=26, max_strings=5000)
+    opts = dict(max_slots=len(insts), max_subspace=args.engine_subspace, max_norb=26, max_strings=5000, max_iter=400)
     small = sorted(insts, key=lambda w: w.ndets)[:2]
     for _ in range(args.warmup):
         with B.Engine(**opts) as e:
@@ -320,7 +320,7 @@ def run_serve(args):
     jobs = [(t, W.make_job(spec, te)) for t, spec, te in trace]
     t_build = time.perf_counter() - t_build
     max_norb = max(w.norb for _, w in jobs)
-    opts = dict(max_slots=64, max_subspace=args.engine_subspace, max_norb=max_norb, max_strings=args.max_strings,
+    opts = dict(max_slots=64, max_subspace=args.engine_subspace, max_norb=max_norb, max_strings=args.max_strings, max_iter=400,
                 hbm_budget_bytes=int(args.budget_gb * 1e9))
     small = sorted((w for _, w in jobs), key=lambda w: w.ndets)[:2]
     for _ in range(args.warmup):
