@@ -137,7 +137,7 @@ def sum_over_ranks(value: float, world: int) -> float:
 def workload_config(wl, precision):
     return {"workload": f"{wl.name}: norb={wl.norb}, nalpha=nbeta={wl.nalpha}, |A|=|B|={wl.A.size:,} "
                         f"Gumbel-top-k strings, {wl.ndets:.2e} determinants, {wl.nroots} root, "
-                        f"{precision} sigma + FP64 defect correction, residual <= {wl.tol:g}",
+                        f"{precision} sigma + FP64-accurate defect correction, residual <= {wl.tol:g}",
             "norb": wl.norb, "nalpha": wl.nalpha, "nbeta": wl.nbeta, "nA": int(wl.A.size), "nB": int(wl.B.size),
             "ndets": int(wl.ndets), "nroots": wl.nroots, "tol": wl.tol, "precision": precision,
             "step": "sbd_create + sbd_davidson + sbd_destroy (one full solve)",
@@ -204,13 +204,20 @@ def run_reference(args):
 # GPU arm
 
 
+def kernel_source_digest() -> str:
+    """sha256 prefix of the alpha-beta pass's source (the per-row device function and its kernel)."""
+    src = open(os.path.join(ROOT, "paper_2601_16637_gb300", "csrc", "sigma.cu")).read()
+    start = src.index("__device__ __forceinline__ void ab_row(")
+    end = src.index("}\n", src.index("__global__ void __launch_bounds__(Threads<T>::value) ab_pass_kernel(")) + 2
+    return hashlib.sha256(src[start:end].encode()).hexdigest()[:16]
+
+
 def traffic_record(kernel: str):
     """dram bytes per launch from the committed ncu summary, if taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    src = os.path.join(ROOT, "paper_2601_16637_gb300", "csrc", "sigma.cu")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    digest = kernel_source_digest()
     for line in open(path):
         parts = line.split()
         if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:
@@ -590,7 +597,9 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == "mixed" else "f64",
+                "scaling": "weak", "vs_baseline": None,
+                # mixed: FP32 sigma, FP32-pair (FP64-accurate) sigma for the defect corrections, FP64 Davidson
+                "dtype": "f32+f32x2+f64" if prec == "mixed" else "f64",
                 "data": "synthetic", "config": workload_config(wl, prec),
                 "parallelism": "replicas" if world > 1 else "single GPU",
                 "solves_per_s": solves_per_s, "sigma_applications_per_step": n_sigma / args.steps,

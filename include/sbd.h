@@ -273,6 +273,24 @@ int sbd_sigma_batched(int n, const sbd_handle *handles, const void *const *c_dev
                       sbd_precision prec, int rows_per_item, void *stream);
 
 /*
+ * Alpha-row sharding (paper Sec. III: the alpha rows of C and sigma are distributed over
+ * processes and the C blocks are passed around a ring).  A block plan fixes output alpha rows
+ * [r0, r1) and source alpha rows [j0, j1) of the handle's instance; sbd_sigma_block adds the
+ * contribution of the source block to the output rows:
+ *   sigma_rows[(ia-r0)*nB + ib] += sum_{ja in [j0,j1), jb} H[(ia,ib),(ja,jb)] c_block[(ja-j0)*nB + jb]
+ * Summed over the blocks of a partition of [0, nA), this is rows [r0, r1) of sbd_sigma (up to the
+ * rounding order of the partial sums).  c_block: device pointer, (j1-j0)*nB elements (float for
+ * SBD_MIXED, double otherwise); sigma_rows: device pointer, (r1-r0)*nB doubles, accumulated (zero
+ * it before the first block).  A plan holds device memory through the handle's allocator and
+ * budget and must be destroyed before the handle; calls on one plan must not overlap.
+ */
+typedef struct sbd_block_plan_s *sbd_block_plan;
+int sbd_block_plan_create(sbd_handle handle, int64_t r0, int64_t r1, int64_t j0, int64_t j1, sbd_block_plan *out);
+int sbd_sigma_block(sbd_block_plan plan, const void *c_block_dev, double *sigma_rows_dev, sbd_precision prec,
+                    void *stream);
+int sbd_block_plan_destroy(sbd_block_plan plan);
+
+/*
  * Batched and served solves.  No counterpart in the paper: an engine runs the
  * Davidson iterations (Sec. II-C, the Eq. 7 preconditioner) of many
  * independent instances ("jobs") together on one device.  Per engine

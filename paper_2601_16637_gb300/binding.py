@@ -113,6 +113,9 @@ _SIGNATURES = {
     "sbd_launch_count": (_i64, []),
     "sbd_sort_strings_noalloc": (_int, [_vp, _i64, _int, _int, _vp, C.POINTER(_i64), _vp]),
     "sbd_sigma_batched": (_int, [_int, _vp, _vp, _vp, _int, _int, _vp]),
+    "sbd_block_plan_create": (_int, [_vp, _i64, _i64, _i64, _i64, C.POINTER(_vp)]),
+    "sbd_sigma_block": (_int, [_vp, _vp, _vp, _int, _vp]),
+    "sbd_block_plan_destroy": (_int, [_vp]),
     "sbd_engine_default_options": (None, [C.POINTER(sbd_engine_options)]),
     "sbd_engine_create": (_int, [C.POINTER(_vp), C.POINTER(sbd_engine_options), _vp]),
     "sbd_engine_destroy": (_int, [_vp]),
@@ -337,6 +340,20 @@ def sbd_sigma_batched(handles, cs, sigmas, precision, rows_per_item: int = 0, st
     xs = (C.c_void_p * max(n, 1))(*[_ptr(x) for x in cs])
     ys = (C.c_void_p * max(n, 1))(*[_ptr(y) for y in sigmas])
     _check(load().sbd_sigma_batched(n, hs, xs, ys, PRECISION[precision], int(rows_per_item), _stream(stream)))
+
+
+def sbd_block_plan_create(handle, r0, r1, j0, j1) -> int:
+    out = C.c_void_p()
+    _check(load().sbd_block_plan_create(handle, int(r0), int(r1), int(j0), int(j1), C.byref(out)), handle)
+    return out.value
+
+
+def sbd_sigma_block(plan, c_block, sigma_rows, precision, stream=None) -> None:
+    _check(load().sbd_sigma_block(plan, _ptr(c_block), _ptr(sigma_rows), PRECISION[precision], _stream(stream)))
+
+
+def sbd_block_plan_destroy(plan) -> None:
+    _check(load().sbd_block_plan_destroy(plan))
 
 
 def sbd_engine_default_options() -> sbd_engine_options:

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 LIB = os.path.join(LIBDIR, "libsbd.so")
-SOURCES = ["api.cu", "strings.cu", "tables.cu", "sigma.cu", "davidson.cu", "noalloc.cu", "engine.cu"]
+SOURCES = ["api.cu", "strings.cu", "tables.cu", "sigma.cu", "davidson.cu", "noalloc.cu", "engine.cu", "shard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

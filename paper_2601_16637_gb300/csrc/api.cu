@@ -220,6 +220,52 @@ int sbd_sigma_batched(int n, const sbd_handle *handles, const void *const *c_dev
     });
 }
 
+}  // extern "C"
+
+struct sbd_block_plan_s {
+    sbd_handle h;
+    BlockPlan *p;
+};
+
+extern "C" {
+
+int sbd_block_plan_create(sbd_handle h, int64_t r0, int64_t r1, int64_t j0, int64_t j1, sbd_block_plan *out)
+{
+    if (!h || !out) return SBD_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guarded(h, [&]() -> int {
+        BlockPlan *p = block_plan_create(h->c, r0, r1, j0, j1);
+        auto *bp = new (std::nothrow) sbd_block_plan_s{h, p};
+        if (!bp) {
+            block_plan_destroy(p);
+            fail(SBD_ERR_OUT_OF_MEMORY, "host allocation failed");
+        }
+        *out = bp;
+        return SBD_OK;
+    });
+}
+
+int sbd_sigma_block(sbd_block_plan bp, const void *c_block_dev, double *sigma_rows_dev, sbd_precision prec,
+                    void *stream)
+{
+    if (!bp || !c_block_dev || !sigma_rows_dev || prec < SBD_FP64 || prec > SBD_F32X2) return SBD_ERR_INVALID_ARG;
+    return guarded(bp->h, [&]() -> int {
+        sigma_block_apply(*bp->p, c_block_dev, sigma_rows_dev, prec, (cudaStream_t)stream);
+        return SBD_OK;
+    });
+}
+
+int sbd_block_plan_destroy(sbd_block_plan bp)
+{
+    if (!bp) return SBD_ERR_INVALID_ARG;
+    const int rc = guarded(bp->h, [&]() -> int {
+        block_plan_destroy(bp->p);
+        return SBD_OK;
+    });
+    delete bp;
+    return rc;
+}
+
 const char *sbd_last_error(sbd_handle h) { return h ? h->c.last_error.c_str() : g_last_error.c_str(); }
 
 int sbd_create(sbd_handle *out, int norb, int nalpha, int nbeta, const double *h, const double *eri,

@@ -77,7 +77,6 @@ struct SpinTables {
     float2 *s_vx2 = nullptr;   // s_v64_sig as FP32 pairs (hi, lo), for the FP32-pair sigma
     float2 *d_vx2 = nullptr;   // d_v64_sig as FP32 pairs
     double *ediag = nullptr;     // [n] same-spin diagonal energies
-    int max_singles = 0;         // longest singles list
     bool alias = false;          // storage owned by the other spin (A == B)
 };
 
@@ -123,6 +122,17 @@ template <typename T>
 T *dalloc_n(Ctx &c, size_t n)
 {
     return static_cast<T *>(dalloc(c, n * sizeof(T) > 0 ? n * sizeof(T) : 16));
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal preconditioner of Davidson (paper Eq. 7): t = r / (sign(d) max(|d|, delta)),
+// d = Hd - theta.  The factor multiplying r is formed as an FP32 reciprocal: a preconditioner only
+// shapes the correction direction (which is then orthogonalised and normalised in FP64), and the
+// FP64 division would cost the FP64 pipe as much as a fifth of the Ritz pass.
+__device__ __forceinline__ double precond_factor(double d, double delta)
+{
+    const double den = (d >= 0.0 ? 1.0 : -1.0) * fmax(fabs(d), delta);
+    return (double)__frcp_rn((float)den);
 }
 
 // ---------------------------------------------------------------------------
@@ -172,6 +182,33 @@ void to_float(const double *in, float *out, int64_t n, cudaStream_t s);
 
 // sigma.cu
 void sigma_prepare(Ctx &c);
+
+// ---------------------------------------------------------------------------
+// row-block sigma for alpha-row sharding (shard.cu, sigma.cu)
+
+// The alpha lists of output rows [r0, r1) restricted to sources in [j0, j1), targets renumbered
+// from j0, in the layouts of SpinTables (canonical singles; padded sigma singles and doubles).
+struct BlockPlan {
+    Ctx *c = nullptr;
+    int64_t r0 = 0, r1 = 0, j0 = 0, j1 = 0;
+    int64_t *s_ptr = nullptr;
+    uint32_t *s_pk = nullptr;
+    int64_t *sig_s_ptr = nullptr, *sig_d_ptr = nullptr;
+    uint32_t *s_pk_sig = nullptr;
+    double *s_v64_sig = nullptr;
+    uint2 *s_pkv32 = nullptr;
+    float2 *s_vx2 = nullptr;
+    int32_t *d_j_sig = nullptr;
+    double *d_v64_sig = nullptr;
+    uint2 *d_jv32 = nullptr;
+    float2 *d_vx2 = nullptr;
+    void *work_t = nullptr;  // [nB][j1 - j0] doubles: the transposed source block
+    std::vector<void *> allocs;
+};
+BlockPlan *block_plan_create(Ctx &c, int64_t r0, int64_t r1, int64_t j0, int64_t j1);
+void block_plan_destroy(BlockPlan *p);
+// sigma_rows[(ia - r0)*nB + ib] += sum over (ja, jb), ja in [j0, j1), of H[(ia,ib),(ja,jb)] cblock[(ja - j0)*nB + jb]
+void sigma_block_apply(BlockPlan &p, const void *cblock, double *sigma_rows, sbd_precision prec, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // batched sigma: many instances in one set of persistent launches (sigma.cu)

@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kBlas) combine_kernel(const double *__restrict
                     const double r = hu[j] - th[j] * u[j];
                     racc[j] += r * r;
                     const double d = hd[i] - th[j];
-                    tc[j * ldo + i] = r / ((d >= 0.0 ? 1.0 : -1.0) * fmax(fabs(d), delta));
+                    tc[j * ldo + i] = r * precond_factor(d, delta);
                 }
             }
     }
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kBlas) resid_partial(const double *__restrict_
         }
 }
 
-// t = (hu - theta u) / (sign(d) max(|d|, delta)), d = Hd - theta   (Eq. 7)
+// t = (hu - theta u) / (sign(d) max(|d|, delta)), d = Hd - theta   (Eq. 7; see precond_factor)
 __global__ void precond_kernel(const double *__restrict__ u, const double *__restrict__ hu,
                                const double *__restrict__ hd, const double *__restrict__ theta, double delta,
                                double *t, int64_t N)
@@ -248,8 +248,7 @@ __global__ void precond_kernel(const double *__restrict__ u, const double *__res
     const double th = *theta;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const double d = hd[i] - th;
-        const double den = (d >= 0.0 ? 1.0 : -1.0) * fmax(fabs(d), delta);
-        t[i] = (hu[i] - th * u[i]) / den;
+        t[i] = (hu[i] - th * u[i]) * precond_factor(d, delta);
     }
 }
 

@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kEThreads) e_ritz_kernel(const Header *hdr, co
             const double dd = d.hd[i] - th;
             d.U[i] = u;
             d.HU[i] = hu;
-            d.TC[i] = r / ((dd >= 0.0 ? 1.0 : -1.0) * fmax(fabs(dd), delta));
+            d.TC[i] = r * precond_factor(dd, delta);
         }
         const double sum = block_sum(racc, red);
         if (threadIdx.x == 0) partial[(int64_t)c * kEPart + 0] = sum;

@@ -1,0 +1,97 @@
+"""Alpha-row sharding of the sigma product over ranks (paper Sec. III, the distributed product).
+
+Rank r owns the alpha rows [bounds[r], bounds[r+1]) of C and of sigma.  The C blocks travel around
+the ring of ranks: at step s rank r holds block (r - s) mod P, adds that block's contribution to its
+own rows, and meanwhile sends the block on to rank r+1 and receives the next one from rank r-1
+(two buffers, so the transfer overlaps the products).  After P steps every rank has met every
+block once, and its rows of sigma are complete.
+
+This module is host logic only.  The block products come from a callable
+`block_sigma(b, c_block, out_rows)` that adds block b's contribution to the rank's rows; on a GPU
+that is sbd_sigma_block through one block plan per source block (`device_block_sigma`).
+"""
+from __future__ import annotations
+
+from typing import Callable, Sequence
+
+
+def row_blocks(n: int, parts: int) -> list[int]:
+    """Boundaries of `parts` contiguous blocks of [0, n) whose sizes differ by at most one."""
+    if parts < 1 or n < parts:
+        raise ValueError("need 1 <= parts <= n")
+    q, r = divmod(n, parts)
+    out = [0]
+    for p in range(parts):
+        out.append(out[-1] + q + (1 if p < r else 0))
+    return out
+
+
+def ring_schedule(rank: int, world: int) -> list[int]:
+    """The source blocks rank `rank` holds at steps 0..world-1 (its own block first)."""
+    return [(rank - s) % world for s in range(world)]
+
+
+class RingSigma:
+    """sigma rows of this rank from its own C rows, with the other ranks' blocks passed around a
+    ring.  bounds: row_blocks(nA, world); row_len: elements per alpha row (nB)."""
+
+    def __init__(self, block_sigma: Callable, bounds: Sequence[int], rank: int, world: int, row_len: int,
+                 group=None):
+        if len(bounds) != world + 1:
+            raise ValueError("bounds must have world + 1 entries")
+        self.block_sigma = block_sigma
+        self.bounds = list(bounds)
+        self.rank, self.world, self.row_len, self.group = rank, world, row_len, group
+        self.steps = []  # (step, block) as processed, for inspection
+
+    def rows(self, b: int) -> int:
+        return self.bounds[b + 1] - self.bounds[b]
+
+    def __call__(self, c_own, out_rows):
+        import torch
+        import torch.distributed as dist
+
+        out_rows.zero_()
+        self.steps = []
+        P, r = self.world, self.rank
+        if P == 1:
+            self.block_sigma(0, c_own, out_rows)
+            self.steps.append((0, 0))
+            return out_rows
+        nmax = max(self.rows(b) for b in range(P)) * self.row_len
+        bufs = [torch.empty(nmax, dtype=c_own.dtype, device=c_own.device) for _ in range(2)]
+        cur, cur_b = c_own, r
+        sched = ring_schedule(r, P)
+        for s in range(P):
+            reqs = []
+            if s < P - 1:
+                nxt_b = sched[s + 1]
+                nxt = bufs[s % 2][: self.rows(nxt_b) * self.row_len]
+                reqs = [dist.isend(cur.contiguous(), (r + 1) % P, group=self.group),
+                        dist.irecv(nxt, (r - 1) % P, group=self.group)]
+            self.block_sigma(cur_b, cur, out_rows)
+            self.steps.append((s, cur_b))
+            for q in reqs:
+                q.wait()
+            if s < P - 1:
+                cur, cur_b = nxt, nxt_b
+        return out_rows
+
+
+def device_block_sigma(handle, bounds: Sequence[int], rank: int, precision, stream=None):
+    """block_sigma for RingSigma on a GPU: one block plan per source block (sbd_block_plan_create),
+    products by sbd_sigma_block.  Returns (callable, close)."""
+    from . import binding as B
+
+    r0, r1 = bounds[rank], bounds[rank + 1]
+    plans = [B.sbd_block_plan_create(handle, r0, r1, bounds[b], bounds[b + 1]) for b in range(len(bounds) - 1)]
+
+    def block_sigma(b, c_block, out_rows):
+        B.sbd_sigma_block(plans[b], c_block, out_rows, precision, stream)
+
+    def close():
+        for p in plans:
+            B.sbd_block_plan_destroy(p)
+        plans.clear()
+
+    return block_sigma, close

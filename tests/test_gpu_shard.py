@@ -1,0 +1,93 @@
+"""Row-block sigma for alpha-row sharding, through the C ABI on one GPU.
+
+For a partition of the alpha rows into P blocks, the contributions of all source blocks to each
+rank's rows (sbd_sigma_block through one block plan per source block) must add up to that rank's
+rows of the full sigma: within FP64 rounding for SBD_FP64 and SBD_F32X2 (and against the oracle),
+within FP32 grouping for SBD_MIXED.  The ranks are emulated one after another in one process;
+nothing waits on anything else.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import SIGMA_FP64_RTOL, medium, rel_maxnorm
+from paper_2601_16637_gb300 import shard
+from paper_2601_16637_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+
+    assert t.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2601_16637_gb300 import build
+
+    build.build()
+    return t
+
+
+@pytest.fixture(scope="module")
+def B(torch):
+    from paper_2601_16637_gb300 import binding
+
+    binding.load()
+    return binding
+
+
+def _rank_rows(torch, B, g, x, prec, parts, r):
+    bounds = shard.row_blocks(g.nA, parts)
+    r0, r1 = bounds[r], bounds[r + 1]
+    out = torch.zeros((r1 - r0) * g.nB, dtype=torch.float64, device="cuda")
+    fn, close = shard.device_block_sigma(g.handle, bounds, r, prec)
+    try:
+        for b in range(parts):
+            fn(b, x[bounds[b] * g.nB: bounds[b + 1] * g.nB], out)
+    finally:
+        close()
+    return out, r0, r1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f32x2", "mixed"])
+@pytest.mark.parametrize("wl", [medium(), medium(norb=11, n=4, nb=3, nA=197, nB=133, seed=12)], ids=["med", "uneq"])
+def test_block_sigma_adds_up_to_the_full_sigma(torch, B, prec, wl):
+    tol = {"fp64": 1e-13, "f32x2": 1e-13, "mixed": 2e-6}[prec]
+    dt = torch.float32 if prec == "mixed" else torch.float64
+    with B.SBD.from_workload(wl) as g:
+        x = torch.from_numpy(W.random_vector(g.N, 41)[0]).to("cuda", dt)
+        full = g.sigma(x, prec).cpu().numpy()
+        for parts in (1, 2, 3):
+            for r in range(parts):
+                out, r0, r1 = _rank_rows(torch, B, g, x, prec, parts, r)
+                ref = full[r0 * g.nB: r1 * g.nB]
+                assert rel_maxnorm(out.cpu().numpy(), ref) <= tol, (parts, r)
+
+
+def test_block_sigma_against_the_oracle_and_a_shared_table_instance(torch, B, oracle_mod):
+    # cfg1: A == B, so the two spins share their tables
+    for wl in (W.config("cfg1"), medium()):
+        with B.SBD.from_workload(wl) as g:
+            o = oracle_mod.Oracle.from_workload(wl)
+            xn = W.random_vector(g.N, 42)[0]
+            ref = o.sigma(xn[None, :])[0]
+            x = torch.from_numpy(xn).cuda()
+            parts = 4
+            got = np.concatenate([_rank_rows(torch, B, g, x, "fp64", parts, r)[0].cpu().numpy() for r in range(parts)])
+            assert rel_maxnorm(got, ref) <= SIGMA_FP64_RTOL
+            o.close()
+
+
+def test_ring_driver_on_one_rank_and_plan_errors(torch, B):
+    wl = medium()
+    with B.SBD.from_workload(wl) as g:
+        x = torch.from_numpy(W.random_vector(g.N, 43)[0]).cuda()
+        bounds = shard.row_blocks(g.nA, 1)
+        fn, close = shard.device_block_sigma(g.handle, bounds, 0, "fp64")
+        ring = shard.RingSigma(fn, bounds, 0, 1, g.nB)
+        out = torch.empty(g.N, dtype=torch.float64, device="cuda")
+        ring(x, out)
+        close()
+        assert rel_maxnorm(out.cpu().numpy(), g.sigma(x, "fp64").cpu().numpy()) <= 1e-15
+        for r0, r1, j0, j1 in [(5, 5, 0, 3), (0, g.nA + 1, 0, 3), (0, 3, -1, 2), (0, 3, 2, 1)]:
+            with pytest.raises(B.SbdError):
+                B.sbd_block_plan_create(g.handle, r0, r1, j0, j1)

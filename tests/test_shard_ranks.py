@@ -1,0 +1,91 @@
+"""Alpha-row sharding of sigma over ranks (paper Sec. III): row partition, ring schedule, and the
+ring exchange with two and three gloo ranks on CPU.  The block products come from the CPU oracle
+(sigma of the vector restricted to the block's rows, by linearity), so the test checks the
+partition and the exchange: every rank must end with exactly its rows of the full sigma."""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+from paper_2601_16637_gb300 import shard  # noqa: E402
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def test_row_blocks_and_ring_schedule():
+    assert shard.row_blocks(10, 3) == [0, 4, 7, 10]
+    assert shard.row_blocks(6, 6) == [0, 1, 2, 3, 4, 5, 6]
+    assert shard.row_blocks(5, 1) == [0, 5]
+    with pytest.raises(ValueError):
+        shard.row_blocks(2, 3)
+    for world in (1, 2, 3, 5):
+        for r in range(world):
+            s = shard.ring_schedule(r, world)
+            assert s[0] == r and sorted(s) == list(range(world))
+            # at every step, the block a rank holds is the one its left neighbour held the step before
+            if world > 1:
+                left = shard.ring_schedule((r - 1) % world, world)
+                assert all(s[k + 1] == left[k] for k in range(world - 1))
+
+
+def _ring_worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+
+    from oracle import oracle as O
+    from paper_2601_16637_gb300 import shard as S
+    from paper_2601_16637_gb300 import workloads as W
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    wl = W.make("ring", 10, 3, 4, 61, 45, 0.2, seed=31)
+    o = O.Oracle.from_workload(wl)
+    nA, nB, N = o.nA, o.nB, o.N
+    x = W.random_vector(N, 5)[0]
+    bounds = S.row_blocks(nA, world)
+    r0, r1 = bounds[rank], bounds[rank + 1]
+    rows = np.arange(r0 * nB, r1 * nB)
+
+    def block_sigma(b, c_block, out_rows):
+        xf = np.zeros(N)
+        xf[bounds[b] * nB: bounds[b + 1] * nB] = c_block.numpy()
+        out_rows += torch.from_numpy(o.sigma_rows(xf[None, :], rows)[0])
+
+    ring = S.RingSigma(block_sigma, bounds, rank, world, nB)
+    out = torch.empty((r1 - r0) * nB, dtype=torch.float64)
+    ring(torch.from_numpy(x[r0 * nB: r1 * nB].copy()), out)
+    ref = o.sigma(x[None, :])[0][r0 * nB: r1 * nB]
+    err = float(np.abs(out.numpy() - ref).max() / np.abs(ref).max())
+    q.put((rank, err, [b for _, b in ring.steps]))
+    dist.barrier()
+    dist.destroy_process_group()
+    o.close()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_ring_sigma_over_gloo_ranks(world, oracle_mod):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_ring_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(world))
+    for rank, err, blocks in res:
+        assert err <= 1e-13
+        assert blocks == shard.ring_schedule(rank, world)
