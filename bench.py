@@ -157,15 +157,17 @@ def oracle_rows_rate(wl, budget_s: float, seed: int = 0):
     x /= np.linalg.norm(x)
     rng = np.random.default_rng(seed)
     threads = O.num_threads()
-    pilot = rng.integers(0, o.N, size=max(8, 2 * threads))
-    t0 = time.perf_counter()
-    o.sigma_rows(x, pilot)
-    per_row = (time.perf_counter() - t0) / pilot.size
-    nrows = int(max(pilot.size, min(200000, budget_s / max(per_row, 1e-9))))
-    rows = rng.integers(0, o.N, size=nrows)
-    t0 = time.perf_counter()
-    o.sigma_rows(x, rows)
-    dt = time.perf_counter() - t0
+    # batches of uniformly drawn rows, each about twice the last, until the budget is spent
+    nrows, dt, batch = 0, 0.0, max(64, 8 * threads)
+    while dt < budget_s:
+        rows = rng.integers(0, o.N, size=batch)
+        t0 = time.perf_counter()
+        o.sigma_rows(x, rows)
+        step = time.perf_counter() - t0
+        nrows += batch
+        dt += step
+        left = budget_s - dt
+        batch = int(min(2 * batch, max(64, batch * left / max(step, 1e-9))))
     o.close()
     return nrows / dt, nrows, dt, threads
 
@@ -544,6 +546,13 @@ def main():
                             else "nominal FP64 1.25 TFLOP/s"))
     tr = traffic_record(f"{dominant}_{p_main}")
     roof["traffic"] = tr
+    # HBM view of the same launch: compulsory bytes (read C, read and write sigma) and, when the
+    # ncu record matches the kernel source, the measured DRAM bytes, against the measured copy peak
+    comp = wl.ndets * (elem + 16.0)
+    roof["hbm"] = {"compulsory_GBs": comp / (ms_dom * 1e-3) / 1e9,
+                   "measured_GBs": (tr / (ms_dom * 1e-3) / 1e9) if tr else None,
+                   "peak_GBs": float(peaks["hbm_gbs"]),
+                   "frac_compulsory": comp / (ms_dom * 1e-3) / 1e9 / float(peaks["hbm_gbs"])}
 
     # sigma-only throughput by precision (sum of the four sigma kernels per vector)
     sigma_rate = {}

@@ -1074,8 +1074,6 @@ SigmaBatch *sigma_batch_create(int max_slots, sbd_precision prec, int R, int max
 void sigma_batch_set(SigmaBatch *b, const SigmaSlot *slots, int n)
 {
     if (n < 0 || n > b->max_slots) fail(SBD_ERR_INVALID_ARG, "batched sigma: too many slots");
-    const int lim_n2 = 0;
-    (void)lim_n2;
     for (int i = 0; i < n; ++i) {
         const Ctx &c = *slots[i].c;
         if (sigma_batch_smem(b->prec, b->R, (int)std::max(c.nA, c.nB), c.norb) > b->smem)

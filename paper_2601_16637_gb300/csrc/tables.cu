@@ -363,7 +363,7 @@ __global__ void sigma_order_kernel(const int64_t *__restrict__ ptr, const int64_
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = ptr[i], e = ptr[i + 1], sb = sig_ptr[i], se = sig_ptr[i + 1];
-        const int L = (int)(e - b), Lp = (int)(se - sb);
+        const int Lp = (int)(se - sb);
         for (int q = 0; q < Lp; ++q) perm[sb + q] = -1;  // slots no entry lands on stay padding
         int count[kBankGroups] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int64_t x = b; x < e; ++x) ++count[j_src[x] & (kBankGroups - 1)];
