@@ -93,6 +93,8 @@ typedef struct {
                                 consecutive iterations to count as converged (default 0: off) */
     int refine_precision;    /* FP64-accurate sigma of the defect corrections of SBD_MIXED solves:
                                 SBD_F32X2 (default) or SBD_FP64 */
+    int restart_keep;        /* Ritz vectors a thick restart keeps; 0 = max(nroots, min(max_subspace -
+                                nroots, max(2 nroots, max_subspace/3))) */
 } sbd_options;
 
 typedef struct {
@@ -282,7 +284,9 @@ int sbd_sigma_batched(int n, const sbd_handle *handles, const void *const *c_dev
  * rounding order of the partial sums).  c_block: device pointer, (j1-j0)*nB elements (float for
  * SBD_MIXED, double otherwise); sigma_rows: device pointer, (r1-r0)*nB doubles, accumulated (zero
  * it before the first block).  A plan holds device memory through the handle's allocator and
- * budget and must be destroyed before the handle; calls on one plan must not overlap.
+ * budget and must be destroyed before the handle; calls on one plan must not overlap.  Errors of
+ * sbd_block_plan_create are reported on the handle, those of the other two on the calling thread
+ * (sbd_last_error(NULL)).
  */
 typedef struct sbd_block_plan_s *sbd_block_plan;
 int sbd_block_plan_create(sbd_handle handle, int64_t r0, int64_t r1, int64_t j0, int64_t j1, sbd_block_plan *out);

@@ -40,7 +40,8 @@ class sbd_options(C.Structure):
     _fields_ = [("delta", C.c_double), ("max_subspace", C.c_int), ("max_iter", C.c_int),
                 ("hbm_budget_bytes", C.c_size_t), ("ecore", C.c_double), ("table_algo", C.c_int),
                 ("verbose", C.c_int), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("timing", C.c_int), ("tol_energy", C.c_double), ("refine_precision", C.c_int)]
+                ("timing", C.c_int), ("tol_energy", C.c_double), ("refine_precision", C.c_int),
+                ("restart_keep", C.c_int)]
 
 
 class sbd_report(C.Structure):
@@ -450,7 +451,7 @@ class SBD:
     def __init__(self, norb, nalpha, nbeta, h, eri, A, B, *, stream=None, allocator: str = "torch",
                  delta: float = 1e-4, max_subspace: int = 0, max_iter: int = 200, hbm_budget_bytes: int = 0,
                  ecore: float = 0.0, table_algo: int = 0, verbose: int = 0, timing: bool = False,
-                 tol_energy: float = 0.0, refine_precision: str = "f32x2"):
+                 tol_energy: float = 0.0, refine_precision: str = "f32x2", restart_keep: int = 0):
         self._opts = sbd_default_options()
         self._opts.delta = delta
         self._opts.max_subspace = max_subspace
@@ -462,6 +463,7 @@ class SBD:
         self._opts.timing = int(bool(timing))
         self._opts.tol_energy = float(tol_energy)
         self._opts.refine_precision = PRECISION[refine_precision]
+        self._opts.restart_keep = int(restart_keep)
         self._alloc = None
         if allocator == "torch":
             self._alloc = _TorchAllocator()

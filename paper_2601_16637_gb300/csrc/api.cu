@@ -249,7 +249,7 @@ int sbd_sigma_block(sbd_block_plan bp, const void *c_block_dev, double *sigma_ro
                     void *stream)
 {
     if (!bp || !c_block_dev || !sigma_rows_dev || prec < SBD_FP64 || prec > SBD_F32X2) return SBD_ERR_INVALID_ARG;
-    return guarded(bp->h, [&]() -> int {
+    return guarded(nullptr, [&]() -> int {  // errors: sbd_last_error(NULL) on this thread
         sigma_block_apply(*bp->p, c_block_dev, sigma_rows_dev, prec, (cudaStream_t)stream);
         return SBD_OK;
     });
@@ -258,7 +258,7 @@ int sbd_sigma_block(sbd_block_plan bp, const void *c_block_dev, double *sigma_ro
 int sbd_block_plan_destroy(sbd_block_plan bp)
 {
     if (!bp) return SBD_ERR_INVALID_ARG;
-    const int rc = guarded(bp->h, [&]() -> int {
+    const int rc = guarded(nullptr, [&]() -> int {
         block_plan_destroy(bp->p);
         return SBD_OK;
     });

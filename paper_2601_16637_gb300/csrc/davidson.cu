@@ -519,7 +519,10 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
         return ((size_t)(2 * ms + 2 * nk + nroots)) * (size_t)N * sizeof(double) + (mixed ? (size_t)N * 4 : 0) +
                (1u << 22);
     };
-    auto keep_for = [&](int ms) { return std::max(nroots, std::min(ms - nroots, std::max(2 * nroots, ms / 3))); };
+    auto keep_for = [&](int ms) {
+        if (c.opt.restart_keep > 0) return std::max(nroots, std::min(ms - nroots, c.opt.restart_keep));
+        return std::max(nroots, std::min(ms - nroots, std::max(2 * nroots, ms / 3)));
+    };
     int nkeep = keep_for(max_sub);
     if (c.opt.hbm_budget_bytes) {
         while (max_sub > 2 * nroots && c.bytes_held + need(max_sub, nkeep) > c.opt.hbm_budget_bytes) {

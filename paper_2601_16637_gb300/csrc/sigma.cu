@@ -52,10 +52,23 @@ struct F2 {
     __host__ __device__ constexpr F2(float h, float l) : hi(h), lo(l) {}
 };
 
+// x = hi + lo to 48 bits.  Done on the integer pipe: hi keeps the sign, the exponent and the top 23
+// mantissa bits of x (truncation), lo is the value of the 29 bits cut off; only |x| outside the FP32
+// normal range takes the FP64 route (FP64 conversions and subtraction run on the FP64 pipe, which on
+// this GPU is ~1/64 of the FP32 rate and would otherwise dominate the staging of pair amplitudes).
 __device__ __forceinline__ F2 f2_split(double x)
 {
-    const float hi = __double2float_rn(x);
-    return F2(hi, __double2float_rn(x - (double)hi));
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int h = (unsigned int)(b >> 32), l = (unsigned int)b;
+    const int e = (int)((h >> 20) & 0x7FFu);  // biased FP64 exponent
+    if (e < 1023 - 126 || e > 1023 + 127) {
+        const float hi = __double2float_rn(x);
+        return F2(hi, __double2float_rn(x - (double)hi));
+    }
+    const unsigned int sign = h & 0x80000000u;
+    const float hi = __uint_as_float(sign | ((unsigned int)(e - 1023 + 127) << 23) | ((h & 0xFFFFFu) << 3) | (l >> 29));
+    const float lo = ldexpf(__uint2float_rn(l & 0x1FFFFFFFu), e - 1023 - 52);
+    return F2(hi, sign ? -lo : lo);
 }
 __device__ __forceinline__ double f2_value(F2 a) { return (double)a.hi + (double)a.lo; }
 

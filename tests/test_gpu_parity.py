@@ -331,6 +331,15 @@ def test_davidson_mixed_matches_fp64(torch, B, med_pair, med_lanczos):
         assert r2.status == 0 and abs(r2.energies[0] - r64.energies[0]) <= EIG_MIXED_ATOL
 
 
+def test_davidson_restart_size_option(torch, B, med_pair, med_lanczos):
+    # a larger thick-restart basis converges to the same roots
+    wl, g, o = med_pair
+    e_ref, _ = med_lanczos
+    with B.SBD.from_workload(wl, restart_keep=12) as g12:
+        res = g12.davidson(nroots=3, tol=1e-8)
+        assert res.status == 0 and np.abs(res.energies - e_ref).max() <= EIG_FP64_ATOL
+
+
 def test_davidson_mixed_three_roots(torch, B, med_pair, med_lanczos):
     wl, g, o = med_pair
     e_ref, _ = med_lanczos
