@@ -315,31 +315,8 @@ def run_batch(args):
     return 0
 
 
-def run_serve(args):
-    """A finite Poisson stream of jobs served by one engine (continuous batching under a memory
-    budget), against a FIFO queue served one job at a time by the serial FP64 path."""
-    import torch
-
-    from paper_2601_16637_gb300 import binding as B
-    from paper_2601_16637_gb300 import workloads as W
-
-    B.load(build_if_missing=True)
-    trace = W.serving_trace(n=args.requests, rate=args.rate, max_strings=args.max_strings)
-    t_build = time.perf_counter()
-    jobs = [(t, W.make_job(spec, te)) for t, spec, te in trace]
-    t_build = time.perf_counter() - t_build
-    max_norb = max(w.norb for _, w in jobs)
-    opts = dict(max_slots=64, max_subspace=args.engine_subspace, max_norb=max_norb, max_strings=args.max_strings, max_iter=400,
-                hbm_budget_bytes=int(args.budget_gb * 1e9))
-    small = sorted((w for _, w in jobs), key=lambda w: w.ndets)[:2]
-    for _ in range(args.warmup):
-        with B.Engine(**opts) as e:
-            for w in small:
-                e.submit(w, tol=w.tol, tol_energy=w.extra["tol_energy"])
-            e.run()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(0)
-    clocks.start()
+def serve_once(B, opts, jobs):
+    """One engine serving the (arrival time, job) trace; returns results, base clock, stats."""
     with B.Engine(**opts) as e:
         base = e.clock()
         ids, i, n = [], 0, len(jobs)
@@ -350,48 +327,91 @@ def run_serve(args):
                 w = jobs[i][1]
                 ids.append(e.submit(w, tol=w.tol, tol_energy=w.extra["tol_energy"]))
                 i += 1
-            if e.stats()["active"] + e.stats()["pending"] > 0:
+            st = e.stats()
+            if st["active"] + st["pending"] > 0:
                 remaining = e.step()
             else:
                 remaining = 0
                 if i < n:
                     time.sleep(max(0.0, min(0.01, jobs[i][0] - (e.clock() - base))))
         results = [e.result(j) for j in ids]
-        stats = e.stats()
+        return results, base, e.stats()
+
+
+def run_serve(args):
+    """A finite Poisson stream of jobs served by one engine (continuous batching under a memory
+    budget), against a FIFO queue served one job at a time by the serial FP64 path, for each of the
+    arrival rates given (the same jobs; only the arrival times scale with the rate)."""
+    import torch
+
+    from paper_2601_16637_gb300 import binding as B
+    from paper_2601_16637_gb300 import workloads as W
+
+    B.load(build_if_missing=True)
+    rates = [float(r) for r in str(args.rates).split(",")] if args.rates else [args.rate]
+    traces = {r: W.serving_trace(n=args.requests, rate=r, max_strings=args.max_strings) for r in rates}
+    t_build = time.perf_counter()
+    specs = traces[rates[0]]
+    built = [W.make_job(spec, te) for _, spec, te in specs]
+    t_build = time.perf_counter() - t_build
+    max_norb = max(w.norb for w in built)
+    opts = dict(max_slots=64, max_subspace=args.engine_subspace, max_norb=max_norb, max_strings=args.max_strings,
+                max_iter=400, hbm_budget_bytes=int(args.budget_gb * 1e9))
+    small = sorted(built, key=lambda w: w.ndets)[:2]
+    for _ in range(args.warmup):
+        with B.Engine(**opts) as e:
+            for w in small:
+                e.submit(w, tol=w.tol, tol_energy=w.extra["tol_energy"])
+            e.run()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    runs = []
+    for r in rates:
+        jobs = [(t, w) for (t, _, _), w in zip(traces[r], built)]
+        results, base, stats = serve_once(B, opts, jobs)
+        arrivals = np.array([t for t, _ in jobs])
+        done = np.array([x["t_done"] - base for x in results])
+        runs.append((r, arrivals, done, results, stats))
     clk = clocks.stop()
-    arrivals = np.array([t for t, _ in jobs])
-    done = np.array([r["t_done"] - base for r in results])
-    lat = done - arrivals
-    span = float(done.max() - arrivals.min())
-    dets_sigma = sum(r["ndets"] * (r["sigma_mixed"] + r["sigma_fp64"]) for r in results)
     # serial FP64 per-instance path: measured service time per job, FIFO queue on the same arrivals
     stream = torch.cuda.current_stream()
     service, dE, st64 = [], 0.0, []
-    for (t, w), r in zip(jobs, results):
+    for w, res in zip(built, runs[0][3]):
         ts, e64, st, _ = serial_fp64(B, w, stream)
         service.append(ts)
         st64.append(st)
-        dE = max(dE, abs(e64 - r["energy"]))
-    fin, tcur = [], 0.0
-    for a, sv in zip(arrivals, service):
-        tcur = max(tcur, a) + sv
-        fin.append(tcur)
-    lat64 = np.array(fin) - arrivals
-    span64 = float(fin[-1] - arrivals.min())
-    extra = {"serving": {"requests": n, "rate_per_s": args.rate, "p50_s": float(np.percentile(lat, 50)),
-                         "p99_s": float(np.percentile(lat, 99)), "makespan_s": span,
-                         "status_counts": {str(k): sum(1 for r in results if r["status"] == k)
-                                           for k in sorted({r["status"] for r in results})},
-                         "max_active": None, "bytes_peak": stats["bytes_peak"], "budget_bytes": opts["hbm_budget_bytes"],
-                         "job_build_s": t_build},
-             "vs_serial_fp64": {"p50_s": float(np.percentile(lat64, 50)), "p99_s": float(np.percentile(lat64, 99)),
-                                "makespan_s": span64, "solves_per_s": n / span64,
-                                "service_s_total": float(sum(service)), "max_abs_dE_Ha": dE,
-                                "statuses": {str(k): st64.count(k) for k in sorted(set(st64))}}}
-    config = {"workload": f"serve: {n} Poisson arrivals at {args.rate:g}/s, norb in {{24,32,40,48,58}}, "
+        dE = max(dE, abs(e64 - res["energy"]))
+    sweep = []
+    n = len(built)
+    for r, arrivals, done, results, stats in runs:
+        lat = done - arrivals
+        span = float(done.max() - arrivals.min())
+        fin, tcur = [], 0.0
+        for a, sv in zip(arrivals, service):
+            tcur = max(tcur, a) + sv
+            fin.append(tcur)
+        lat64 = np.array(fin) - arrivals
+        span64 = float(fin[-1] - arrivals.min())
+        sweep.append({"rate_per_s": r, "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                      "makespan_s": span, "solves_per_s": n / span, "bytes_peak": stats["bytes_peak"],
+                      "status_counts": {str(k): sum(1 for x in results if x["status"] == k)
+                                        for k in sorted({x["status"] for x in results})},
+                      "serial_fp64": {"p50_s": float(np.percentile(lat64, 50)), "p99_s": float(np.percentile(lat64, 99)),
+                                      "makespan_s": span64, "solves_per_s": n / span64}})
+    r0, arrivals, done, results, stats = runs[0]
+    span = float(done.max() - arrivals.min())
+    dets_sigma = sum(x["ndets"] * (x["sigma_mixed"] + x["sigma_fp64"]) for x in results)
+    extra = {"serving": {"requests": n, "rate_per_s": r0, "p50_s": sweep[0]["p50_s"], "p99_s": sweep[0]["p99_s"],
+                         "makespan_s": span, "status_counts": sweep[0]["status_counts"],
+                         "bytes_peak": stats["bytes_peak"], "budget_bytes": opts["hbm_budget_bytes"],
+                         "job_build_s": t_build, "sweep": sweep},
+             "vs_serial_fp64": {**sweep[0]["serial_fp64"], "service_s_total": float(sum(service)),
+                                "max_abs_dE_Ha": dE, "statuses": {str(k): st64.count(k) for k in sorted(set(st64))}}}
+    config = {"workload": f"serve: {n} Poisson arrivals at {r0:g}/s, norb in {{24,32,40,48,58}}, "
                           f"nalpha=nbeta=round(norb/3), |A|=|B| log-uniform in [300,{args.max_strings}], own "
-                          f"integrals each; 1 root, mixed sigma, residual <= {jobs[0][1].tol:g} and Ritz-value change <= 1e-6 Ha; "
-                          f"admission budget {args.budget_gb:g} GB",
+                          f"integrals each; 1 root, mixed sigma, residual <= {built[0].tol:g} and Ritz-value change "
+                          f"<= 1e-6 Ha; admission budget {args.budget_gb:g} GB",
               "step": "the whole trace (arrival of the first job to completion of the last)",
               "l2": "inputs larger than L2"}
     args.steps = 1
@@ -413,6 +433,7 @@ def main():
     ap.add_argument("--batch-n", type=int, default=64, help="instances of the batch64 workload")
     ap.add_argument("--requests", type=int, default=40, help="jobs of the serve workload")
     ap.add_argument("--rate", type=float, default=20.0, help="arrivals per second of the serve workload")
+    ap.add_argument("--rates", default="", help="comma-separated arrival rates for a serve sweep (first one reported)")
     ap.add_argument("--max-strings", type=int, default=5000, help="largest |A| = |B| of the serve workload")
     ap.add_argument("--budget-gb", type=float, default=160.0, help="engine admission budget of the serve workload")
     ap.add_argument("--engine-subspace", type=int, default=20, help="Davidson basis per job in the engine")

@@ -313,7 +313,8 @@ int sbd_block_plan_destroy(sbd_block_plan plan);
  * result is then checked with one FP64 sigma of the Ritz vector, whose FP64
  * residual must also be <= tol (else the job iterates on with a halved mixed
  * threshold).  Reported energy = FP64 Rayleigh quotient + ecore.
- * Orthogonalisation: classical Gram-Schmidt, always two passes; thick restart
+ * Orthogonalisation: classical Gram-Schmidt with a second pass when the first removed more than
+ * half of the squared norm (the DGKS criterion, decided per job on the device); thick restart
  * to nkeep = max(2, max_subspace/3) Ritz vectors.
  */
 typedef struct sbd_engine_s *sbd_engine;

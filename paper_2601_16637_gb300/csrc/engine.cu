@@ -15,7 +15,8 @@
 //
 // One engine iteration = graph A (Rayleigh-Ritz: Jacobi per slot, Ritz vector,
 // residual, preconditioned correction) and graph B (thick-restart compression,
-// two-pass classical Gram-Schmidt of the correction, normalisation, batched
+// classical Gram-Schmidt of the correction (a second pass where the first removed more than
+// half of its squared norm), normalisation, batched
 // mixed sigma of the new vector, extension of the projected matrix; and for
 // jobs that have converged in mixed precision, the batched FP64 sigma of the
 // Ritz vector with its Rayleigh quotient and residual).  Both graphs are
@@ -61,7 +62,8 @@ enum : int {
     kRedUU = 5,      // u . u
     kRedTheta64 = 6, // FP64 Rayleigh quotient
     kRedR64 = 7,     // ||H64 u - theta64 u||^2
-    kRedCount = 8
+    kRedNeed2 = 8,   // 1 when the first Gram-Schmidt pass removed more than half of |t|^2
+    kRedCount = 9
 };
 
 struct SlotDev {
@@ -184,6 +186,7 @@ __global__ void __launch_bounds__(kEThreads) e_dots_kernel(const Header *hdr, co
         const SlotDev &d = slots[chunk_slot[c]];
         const int mask = MODE == 2 ? kCheck : kGrow;
         if (!(d.kind & mask)) continue;
+        if (MODE == 0 && !NORM && d.red[kRedNeed2] == 0.0) continue;  // second Gram-Schmidt pass not needed
         const int ke = keff(d);
         const int cnt = MODE == 0 ? ke : (MODE == 1 ? ke + 1 : 1);
         const double *X = MODE == 2 ? d.U : d.V;
@@ -223,7 +226,8 @@ __global__ void __launch_bounds__(kEThreads) e_dots_kernel(const Header *hdr, co
 }
 
 // TC -= sum_a coef[a] V[a] (a < keff) for kGrow slots; with NORM, partial[c][kNorm] = |TC|^2 after
-template <bool NORM>
+// SECOND: the second Gram-Schmidt pass, only for slots whose first pass asked for it
+template <bool NORM, bool SECOND>
 __global__ void __launch_bounds__(kEThreads) e_axpy_kernel(const Header *hdr, const SlotDev *slots,
                                                           const int *chunk_slot, const int64_t *chunk_off,
                                                           double *partial)
@@ -234,6 +238,7 @@ __global__ void __launch_bounds__(kEThreads) e_axpy_kernel(const Header *hdr, co
     for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
         const SlotDev &d = slots[chunk_slot[c]];
         if (!(d.kind & kGrow)) continue;
+        if (SECOND && d.red[kRedNeed2] == 0.0) continue;
         const int ke = keff(d);
         __syncthreads();
         for (int a = threadIdx.x; a < ke; a += kEThreads) cs[a] = d.coef[a];
@@ -263,7 +268,7 @@ __global__ void __launch_bounds__(kEThreads) e_axpy_kernel(const Header *hdr, co
 // Per-slot reduction of the chunk partial sums in a fixed order (lane l sums chunks l, l+32, ...
 // of the slot, then a butterfly over the lanes); one warp per output.  What is reduced and where
 // it goes depends on the phase:
-enum : int { kFinRitz, kFinGS1, kFinGS2, kFinAfter, kFinExtend, kFinCheck1, kFinCheck2 };
+enum : int { kFinRitz, kFinGS1, kFinAfter1, kFinGS2, kFinAfter, kFinExtend, kFinCheck1, kFinCheck2 };
 
 __global__ void e_final_kernel(const Header *hdr, SlotDev *slots, const double *partial, int phase)
 {
@@ -272,12 +277,14 @@ __global__ void e_final_kernel(const Header *hdr, SlotDev *slots, const double *
     const SlotDev d = slots[s];
     const int mask = (phase == kFinRitz) ? kRitz : ((phase == kFinCheck1 || phase == kFinCheck2) ? kCheck : kGrow);
     if (!(d.kind & mask)) return;
+    if ((phase == kFinGS2 || phase == kFinAfter) && d.red[kRedNeed2] == 0.0) return;
     const int ke = keff(d);
     int cnt = 0;  // dot outputs 0..cnt-1
     bool norm = false;
     switch (phase) {
     case kFinRitz: cnt = 1; break;
     case kFinGS1: cnt = ke; norm = true; break;
+    case kFinAfter1: norm = true; break;
     case kFinGS2: cnt = ke; break;
     case kFinAfter: norm = true; break;
     case kFinExtend: cnt = ke + 1; break;
@@ -305,8 +312,11 @@ __global__ void e_final_kernel(const Header *hdr, SlotDev *slots, const double *
     case kFinGS2:
         for (int a = 0; a < ke; ++a) d.coef[a] = out[a];
         break;
+    case kFinAfter1:
     case kFinAfter: {
         const double before = d.red[kRedBefore], after = out[kNorm];
+        // a second pass when the first removed more than half of |t|^2 (the DGKS criterion)
+        if (phase == kFinAfter1) d.red[kRedNeed2] = (ke > 0 && !(after > 0.5 * before)) ? 1.0 : 0.0;
         d.red[kRedAfter] = after;
         // keep the correction unless Gram-Schmidt removed all but 1e-10 of its norm
         const bool keep = after > 1e-20 * before && isfinite(after) && after > 0.0;
@@ -964,13 +974,15 @@ void sbd_engine_s::capture()
     SBD_LAUNCH("e_dots_kernel");
     e_final_kernel<<<nsl, 256, 0, stream>>>(hd, sd, partial, kFinGS1);
     SBD_LAUNCH("e_final_kernel");
-    e_axpy_kernel<false><<<gv, kEThreads, 0, stream>>>(hd, sd, cs, co, partial);
+    e_axpy_kernel<true, false><<<gv, kEThreads, 0, stream>>>(hd, sd, cs, co, partial);
     SBD_LAUNCH("e_axpy_kernel");
+    e_final_kernel<<<nsl, 256, 0, stream>>>(hd, sd, partial, kFinAfter1);
+    SBD_LAUNCH("e_final_kernel");
     e_dots_kernel<0, false><<<gv, kEThreads, 0, stream>>>(hd, sd, cs, co, partial);
     SBD_LAUNCH("e_dots_kernel");
     e_final_kernel<<<nsl, 256, 0, stream>>>(hd, sd, partial, kFinGS2);
     SBD_LAUNCH("e_final_kernel");
-    e_axpy_kernel<true><<<gv, kEThreads, 0, stream>>>(hd, sd, cs, co, partial);
+    e_axpy_kernel<true, true><<<gv, kEThreads, 0, stream>>>(hd, sd, cs, co, partial);
     SBD_LAUNCH("e_axpy_kernel");
     e_final_kernel<<<nsl, 256, 0, stream>>>(hd, sd, partial, kFinAfter);
     SBD_LAUNCH("e_final_kernel");

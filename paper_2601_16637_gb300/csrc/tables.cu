@@ -357,14 +357,62 @@ __global__ void ediag_kernel(const uint64_t *S, int64_t n, int norb, const doubl
 // Entries are first ranked as rounds "rank 0 of every target residue mod 8, rank 1 of every
 // residue, ...", so that consecutive entries in that order have distinct residues where the
 // residue counts allow; each phase then receives a run of consecutive positions.
+// round-order position q of a list of Lp slots -> slot: in a chunk of Lc slots (32, or what is left of
+// a short list) m = Lc/4 lanes each fetch 4 slots, and phase u gathers slot 4*l + u of every lane l;
+// position m*u + l goes to slot 4*l + u, so each phase reads m consecutive round-order positions
+__device__ __forceinline__ int slot_of(int q, int Lp)
+{
+    const int chunk = q / 32, within = q % 32;
+    const int m = min(32, Lp - chunk * 32) / 4;
+    return chunk * 32 + 4 * (within % m) + within / m;
+}
+
+// Singles lists, where the gathers read two tables: staged amplitudes by target j and coefficient
+// rows by key = 2*code + neg (16-byte rows, bank group = index mod 8).  Each phase of m positions is
+// filled greedily: first entries whose target and key residues are both new to the phase, then
+// entries with one new residue, then any.  Lists longer than kJointMax keep the target-only order.
+constexpr int kJointMax = 1024;
+__device__ bool joint_order(int64_t b, int64_t e, int64_t sb, int Lp, const int32_t *__restrict__ j_src,
+                            const uint32_t *__restrict__ pk, int64_t *perm)
+{
+    const int L = (int)(e - b);
+    if (L > kJointMax) return false;
+    uint32_t taken[kJointMax / 32];
+    for (int w = 0; w < (L + 31) / 32; ++w) taken[w] = 0u;
+    int q = 0;
+    while (q < L) {
+        const int chunk = q / 32;
+        const int m = min(32, Lp - chunk * 32) / 4;
+        const int phase_end = min(L, q + m - (q - chunk * 32) % m);  // end of the phase q lies in
+        unsigned int usedJ = 0u, usedK = 0u;
+        for (int pass = 0; pass < 3 && q < phase_end; ++pass)
+            for (int x = 0; x < L && q < phase_end; ++x) {
+                if (taken[x >> 5] >> (x & 31) & 1u) continue;
+                const unsigned int bj = 1u << (j_src[b + x] & (kBankGroups - 1));
+                const unsigned int bk = 1u << ((pk[b + x] >> kPackKeyShift) & (kBankGroups - 1));
+                const bool ok = pass == 0 ? !(usedJ & bj) && !(usedK & bk)
+                                          : (pass == 1 ? (!(usedJ & bj) || !(usedK & bk)) : true);
+                if (!ok) continue;
+                taken[x >> 5] |= 1u << (x & 31);
+                usedJ |= bj;
+                usedK |= bk;
+                perm[sb + slot_of(q, Lp)] = b + x;
+                ++q;
+            }
+    }
+    return true;
+}
+
 // perm[sig_ptr[i] + slot] = index of the canonical entry, or -1 for padding.  One thread per source.
+// pk (singles only): packed entries, for the joint target/key order.
 __global__ void sigma_order_kernel(const int64_t *__restrict__ ptr, const int64_t *__restrict__ sig_ptr, int64_t n,
-                                   const int32_t *__restrict__ j_src, int64_t *perm)
+                                   const int32_t *__restrict__ j_src, const uint32_t *__restrict__ pk, int64_t *perm)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = ptr[i], e = ptr[i + 1], sb = sig_ptr[i], se = sig_ptr[i + 1];
         const int Lp = (int)(se - sb);
         for (int q = 0; q < Lp; ++q) perm[sb + q] = -1;  // slots no entry lands on stay padding
+        if (pk && joint_order(b, e, sb, Lp, j_src, pk, perm)) continue;
         int count[kBankGroups] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int64_t x = b; x < e; ++x) ++count[j_src[x] & (kBankGroups - 1)];
         int seen[kBankGroups] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -374,13 +422,7 @@ __global__ void sigma_order_kernel(const int64_t *__restrict__ ptr, const int64_
             int q = 0;  // position in round order
 #pragma unroll
             for (int w = 0; w < kBankGroups; ++w) q += min(count[w], t) + ((w < r && count[w] > t) ? 1 : 0);
-            // round-order position q -> slot: in a chunk of Lc slots (32, or what is left of a
-            // short list) m = Lc/4 lanes each fetch 4 slots, and phase u gathers slot 4*l + u of
-            // every lane l; position m*u + l goes to slot 4*l + u, so each phase reads m
-            // consecutive round-order positions
-            const int chunk = q / 32, within = q % 32;
-            const int m = min(32, Lp - chunk * 32) / 4;
-            perm[sb + chunk * 32 + 4 * (within % m) + within / m] = x;
+            perm[sb + slot_of(q, Lp)] = x;
         }
     }
 }
@@ -567,7 +609,7 @@ void build_tables(Ctx &c, int spin)
     int64_t *perm = dalloc_n<int64_t>(c, (size_t)std::max<int64_t>(std::max(t.sig_ns, t.sig_nd), 1));
     const int ob = blocks_for(n, 128);
     if (t.sig_ns) {
-        sigma_order_kernel<<<ob, 128, 0, c.stream>>>(t.s_ptr, t.sig_s_ptr, n, t.s_j, perm);
+        sigma_order_kernel<<<ob, 128, 0, c.stream>>>(t.s_ptr, t.sig_s_ptr, n, t.s_j, t.s_pk, perm);
         SBD_LAUNCH("sigma_order_kernel(singles)");
         const int gb = blocks_for(t.sig_ns, 256, 16384);
         gather_kernel<uint32_t><<<gb, 256, 0, c.stream>>>(t.s_pk, perm, t.s_pk_sig, t.sig_ns);
@@ -579,7 +621,7 @@ void build_tables(Ctx &c, int spin)
         SBD_LAUNCH("split_kernel(singles)");
     }
     if (t.sig_nd) {
-        sigma_order_kernel<<<ob, 128, 0, c.stream>>>(t.d_ptr, t.sig_d_ptr, n, t.d_j, perm);
+        sigma_order_kernel<<<ob, 128, 0, c.stream>>>(t.d_ptr, t.sig_d_ptr, n, t.d_j, nullptr, perm);
         SBD_LAUNCH("sigma_order_kernel(doubles)");
         const int gb = blocks_for(t.sig_nd, 256, 16384);
         gather_kernel<int32_t><<<gb, 256, 0, c.stream>>>(t.d_j, perm, t.d_j_sig, t.sig_nd);

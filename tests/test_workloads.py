@@ -47,3 +47,31 @@ def test_deterministic_by_seed():
     c = W.make("x", 16, 5, 5, 100, 100, 0.35, seed=1)
     d = W.make("x", 16, 5, 5, 100, 100, 0.35, seed=2)
     assert not np.array_equal(c.A, d.A)
+
+
+def test_batched_workload_shapes():
+    insts = W.batch_instances(6, seed=4)
+    assert len(insts) == 6
+    for w in insts:
+        assert w.norb in (16, 20, 24, 26) and w.nalpha == w.nbeta == round(w.norb / 3)
+        full = math.comb(w.norb, w.nalpha)
+        assert 1 <= w.A.size <= min(5000, full) and 1 <= w.B.size <= min(5000, full)
+        assert w.A.size >= min(500, full) and w.B.size >= min(500, full)
+        assert len(set(w.A.tolist())) == w.A.size
+        assert w.tol == 1e-4 and w.extra["tol_energy"] == 1e-6
+    # own integrals per instance, reproducible
+    same = [(a, b) for i, a in enumerate(insts) for b in insts[i + 1:] if a.norb == b.norb]
+    assert all(not np.allclose(a.h, b.h) for a, b in same)
+    again = W.batch_instances(6, seed=4)
+    assert all(np.array_equal(a.A, b.A) and np.array_equal(a.eri, b.eri) for a, b in zip(insts, again))
+
+
+def test_serving_trace_scales_arrivals_only():
+    slow, fast = W.serving_trace(n=30, rate=1.0), W.serving_trace(n=30, rate=20.0)
+    assert [s for _, s, _ in slow] == [s for _, s, _ in fast]
+    t1 = np.array([t for t, _, _ in slow])
+    t20 = np.array([t for t, _, _ in fast])
+    assert np.all(np.diff(t1) > 0) and np.allclose(t1, 20.0 * t20)
+    for _, spec, tol_e in fast:
+        assert spec["norb"] in (24, 32, 40, 48, 58) and spec["nalpha"] == round(spec["norb"] / 3)
+        assert 300 <= spec["nA"] <= 20000 and spec["nA"] == spec["nB"] and tol_e == 1e-6
