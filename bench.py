@@ -207,11 +207,16 @@ def run_reference(args):
 
 
 def kernel_source_digest() -> str:
-    """sha256 prefix of the alpha-beta pass's source (the per-row device function and its kernel)."""
-    src = open(os.path.join(ROOT, "paper_2601_16637_gb300", "csrc", "sigma.cu")).read()
+    """sha256 prefix of the alpha-beta pass's source (the per-row device function and its kernel) and of
+    the code that orders its sigma lists (the order decides which rows of C it gathers when)."""
+    csrc = os.path.join(ROOT, "paper_2601_16637_gb300", "csrc")
+    src = open(os.path.join(csrc, "sigma.cu")).read()
     start = src.index("__device__ __forceinline__ void ab_row(")
-    end = src.index("}\n", src.index("__global__ void __launch_bounds__(Threads<T>::value) ab_pass_kernel(")) + 2
-    return hashlib.sha256(src[start:end].encode()).hexdigest()[:16]
+    end = src.index("\n}\n", src.index("__global__ void __launch_bounds__(Threads<T>::value) ab_pass_kernel(")) + 3
+    tab = open(os.path.join(csrc, "tables.cu")).read()
+    t0 = tab.index("__device__ __forceinline__ int slot_of(")
+    t1 = tab.index("\n}\n", tab.index("__global__ void sigma_order_kernel(")) + 3
+    return hashlib.sha256((src[start:end] + tab[t0:t1]).encode()).hexdigest()[:16]
 
 
 def traffic_record(kernel: str):

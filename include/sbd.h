@@ -91,8 +91,9 @@ typedef struct {
     int timing;              /* nonzero: time every sigma kernel with CUDA events (sbd_kernel_times) */
     double tol_energy;       /* > 0: a root also needs |theta_k - theta_(k-1)| <= tol_energy between
                                 consecutive iterations to count as converged (default 0: off) */
-    int refine_precision;    /* FP64-accurate sigma of the defect corrections of SBD_MIXED solves:
-                                SBD_F32X2 (default) or SBD_FP64 */
+    int refine_precision;    /* FP64-accurate arithmetic of SBD_MIXED solves: SBD_F32X2 (default; the
+                                defect-correction sigma and the vector dot products, axpys and Ritz
+                                combinations in FP32 pairs) or SBD_FP64 (both on the FP64 pipe) */
     int restart_keep;        /* Ritz vectors a thick restart keeps; 0 = max(nroots, min(max_subspace -
                                 nroots, max(2 nroots, max_subspace/3))) */
 } sbd_options;
@@ -203,8 +204,10 @@ int sbd_sigma(sbd_handle handle, const void *c_dev, double *sigma_dev, int nvec,
  *   prec        SBD_FP64; SBD_F32X2 (every sigma FP64-accurate on the FP32 pipe);
  *               or SBD_MIXED: mixed-precision sigma for the bulk of the iterations
  *               with FP64-accurate defect correction (sbd_options.refine_precision;
- *               the converged residual is always FP64-accurate); orthogonalisation,
- *               the projected eigenproblem, residuals and energies stay FP64
+ *               the converged residual is always FP64-accurate).  Vectors, the projected
+ *               eigenproblem, residuals and energies stay FP64; with SBD_F32X2 (the whole
+ *               solve, or refine_precision of a mixed one) the vector kernels compute their
+ *               sums in FP32 pairs (48-bit products, one FP64 rounding per stored value)
  *   energies_host  nroots doubles (ascending), ecore included
  *   vecs        NULL, or host or device pointer for [nroots][nA*nB] doubles
  *   residuals_host NULL or nroots doubles
@@ -293,6 +296,35 @@ int sbd_block_plan_create(sbd_handle handle, int64_t r0, int64_t r1, int64_t j0,
 int sbd_sigma_block(sbd_block_plan plan, const void *c_block_dev, double *sigma_rows_dev, sbd_precision prec,
                     void *stream);
 int sbd_block_plan_destroy(sbd_block_plan plan);
+
+/*
+ * Alpha-row-sharded Davidson (paper Sec. III: the distributed eigensolver).  Every rank calls
+ * sbd_davidson_sharded on its own handle of the same instance, with the same bounds (world + 1
+ * alpha-row boundaries, bounds[0] = 0, bounds[world] = nA, increasing) and its own rank; it holds
+ * rows [bounds[rank], bounds[rank+1]) of every Davidson vector.  Sigma products run the ring of
+ * sbd_sigma_block over the blocks; dot products, norms and the searches for the initial and the
+ * sign-fixing components are summed over the ranks with allreduce_sum, so every rank takes the same
+ * decisions and returns the same energies.  vecs_rows (NULL or host or device memory) receives this
+ * rank's rows of the eigenvectors, [nroots][(bounds[rank+1]-bounds[rank])*nB].
+ * Callbacks (called from the thread that called sbd_davidson_sharded, in the same order on every
+ * rank; nonzero return = failure, reported as SBD_ERR_CUDA):
+ *   allreduce_sum(ctx, buf, n): replace the n host doubles in buf by their sum over the ranks;
+ *   ring_exchange(ctx, send, send_bytes, recv, recv_bytes, stream): send the device buffer `send` to
+ *     rank (rank+1) mod world and receive into the device buffer `recv` from rank (rank-1) mod world;
+ *     work on `stream` before the call is complete when it is made, and `recv` must hold the data
+ *     when the callback returns.
+ */
+typedef struct {
+    int rank, world;
+    void *ctx;
+    int (*allreduce_sum)(void *ctx, double *buf, int n);
+    int (*ring_exchange)(void *ctx, const void *send, size_t send_bytes, void *recv, size_t recv_bytes,
+                         void *stream);
+} sbd_comm;
+
+int sbd_davidson_sharded(sbd_handle handle, const int64_t *bounds, const sbd_comm *comm, int nroots, double tol,
+                         sbd_precision prec, double *energies_host, double *vecs_rows, double *residuals_host,
+                         sbd_report *report);
 
 /*
  * Batched and served solves.  No counterpart in the paper: an engine runs the

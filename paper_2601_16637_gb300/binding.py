@@ -82,6 +82,15 @@ class sbd_engine_stats(C.Structure):
         return d
 
 
+ALLREDUCE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_double), C.c_int)
+RING_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class sbd_comm(C.Structure):
+    _fields_ = [("rank", C.c_int), ("world", C.c_int), ("ctx", C.c_void_p), ("allreduce_sum", ALLREDUCE_FN),
+                ("ring_exchange", RING_FN)]
+
+
 class SbdError(RuntimeError):
     def __init__(self, code: int, message: str):
         super().__init__(f"{STATUS.get(code, code)}: {message}")
@@ -114,6 +123,8 @@ _SIGNATURES = {
     "sbd_launch_count": (_i64, []),
     "sbd_sort_strings_noalloc": (_int, [_vp, _i64, _int, _int, _vp, C.POINTER(_i64), _vp]),
     "sbd_sigma_batched": (_int, [_int, _vp, _vp, _vp, _int, _int, _vp]),
+    "sbd_davidson_sharded": (_int, [_vp, _vp, C.POINTER(sbd_comm), _int, _dbl, _int, _vp, _vp, _vp,
+                                    C.POINTER(sbd_report)]),
     "sbd_block_plan_create": (_int, [_vp, _i64, _i64, _i64, _i64, C.POINTER(_vp)]),
     "sbd_sigma_block": (_int, [_vp, _vp, _vp, _int, _vp]),
     "sbd_block_plan_destroy": (_int, [_vp]),
@@ -341,6 +352,18 @@ def sbd_sigma_batched(handles, cs, sigmas, precision, rows_per_item: int = 0, st
     xs = (C.c_void_p * max(n, 1))(*[_ptr(x) for x in cs])
     ys = (C.c_void_p * max(n, 1))(*[_ptr(y) for y in sigmas])
     _check(load().sbd_sigma_batched(n, hs, xs, ys, PRECISION[precision], int(rows_per_item), _stream(stream)))
+
+
+def sbd_davidson_sharded(handle, bounds, comm: "sbd_comm", nroots: int, tol: float, precision, energies,
+                         vecs_rows=None, residuals=None) -> tuple[int, sbd_report]:
+    """One rank of an alpha-row-sharded solve; comm carries rank, world and the callbacks."""
+    b = np.ascontiguousarray(bounds, dtype=np.int64)
+    rep = sbd_report()
+    rc = load().sbd_davidson_sharded(handle, _ptr(b), C.byref(comm), int(nroots), float(tol), PRECISION[precision],
+                                     _ptr(energies), _ptr(vecs_rows) if vecs_rows is not None else None,
+                                     _ptr(residuals) if residuals is not None else None, C.byref(rep))
+    _check(rc, handle)
+    return rc, rep
 
 
 def sbd_block_plan_create(handle, r0, r1, j0, j1) -> int:

@@ -507,6 +507,53 @@ int sbd_davidson(sbd_handle h, int nroots, double tol, sbd_precision prec, doubl
     });
 }
 
+int sbd_davidson_sharded(sbd_handle h, const int64_t *bounds, const sbd_comm *comm, int nroots, double tol,
+                         sbd_precision prec, double *energies_host, double *vecs_rows, double *residuals_host,
+                         sbd_report *report)
+{
+    if (!h || !bounds || !comm || !energies_host || prec < SBD_FP64 || prec > SBD_F32X2) return SBD_ERR_INVALID_ARG;
+    return guarded(h, [&]() -> int {
+        Ctx &c = h->c;
+        ShardCtx sh;
+        sh.rank = comm->rank;
+        sh.world = comm->world;
+        sh.comm = *comm;
+        if (sh.world < 1 || sh.rank < 0 || sh.rank >= sh.world || sh.world > c.nA)
+            fail(SBD_ERR_INVALID_ARG, "sharded solve: rank/world out of range");
+        if (sh.world > 1 && (!comm->allreduce_sum || !comm->ring_exchange))
+            fail(SBD_ERR_INVALID_ARG, "sharded solve: communication callbacks missing");
+        sh.bounds.assign(bounds, bounds + sh.world + 1);
+        if (sh.bounds[0] != 0 || sh.bounds[sh.world] != c.nA)
+            fail(SBD_ERR_INVALID_ARG, "sharded solve: bounds must run from 0 to nA");
+        int64_t maxrows = 0;
+        for (int b = 0; b < sh.world; ++b) {
+            if (sh.bounds[b + 1] <= sh.bounds[b]) fail(SBD_ERR_INVALID_ARG, "sharded solve: empty or decreasing block");
+            maxrows = std::max(maxrows, sh.bounds[b + 1] - sh.bounds[b]);
+        }
+        auto cleanup = [&]() {
+            for (BlockPlan *p : sh.plans) block_plan_destroy(p);
+            sh.plans.clear();
+            for (void *&q : sh.ring)
+                if (q) {
+                    dfree(c, q);
+                    q = nullptr;
+                }
+        };
+        try {
+            for (int b = 0; b < sh.world; ++b)
+                sh.plans.push_back(block_plan_create(c, sh.row0(), sh.row0() + sh.rows(), sh.bounds[b], sh.bounds[b + 1]));
+            if (sh.world > 1)
+                for (void *&q : sh.ring) q = dalloc(c, sizeof(double) * (size_t)maxrows * (size_t)c.nB);
+            const int rc = davidson(c, nroots, tol, prec, energies_host, vecs_rows, residuals_host, report, &sh);
+            cleanup();
+            return rc;
+        } catch (...) {
+            cleanup();
+            throw;
+        }
+    });
+}
+
 int sbd_kernel_times(sbd_handle h, double *ms_host, int64_t *launches_host, int reset)
 {
     if (!h) return SBD_ERR_INVALID_ARG;

@@ -208,7 +208,9 @@ struct BlockPlan {
 BlockPlan *block_plan_create(Ctx &c, int64_t r0, int64_t r1, int64_t j0, int64_t j1);
 void block_plan_destroy(BlockPlan *p);
 // sigma_rows[(ia - r0)*nB + ib] += sum over (ja, jb), ja in [j0, j1), of H[(ia,ib),(ja,jb)] cblock[(ja - j0)*nB + jb]
-void sigma_block_apply(BlockPlan &p, const void *cblock, double *sigma_rows, sbd_precision prec, cudaStream_t s);
+// x64_rows (optional, mixed precision): FP64 amplitudes of the output rows, for the diagonal term
+void sigma_block_apply(BlockPlan &p, const void *cblock, double *sigma_rows, sbd_precision prec, cudaStream_t s,
+                       const double *x64_rows = nullptr);
 
 // ---------------------------------------------------------------------------
 // batched sigma: many instances in one set of persistent launches (sigma.cu)
@@ -241,7 +243,22 @@ void sigma_apply(Ctx &c, const void *cvec, double *svec, sbd_precision prec, cud
                  const double *c64 = nullptr);
 
 // davidson.cu
+// A rank of an alpha-row-sharded solve: its rows [bounds[rank], bounds[rank+1]) of every vector,
+// one block plan per source block, two ring buffers and the caller's communication callbacks.
+struct ShardCtx {
+    int rank = 0, world = 1;
+    std::vector<int64_t> bounds;    // world + 1 alpha-row boundaries
+    std::vector<BlockPlan *> plans; // plans[b]: this rank's rows, source block b
+    void *ring[2] = {nullptr, nullptr};
+    sbd_comm comm{};
+    int64_t row0() const { return bounds[rank]; }
+    int64_t rows() const { return bounds[rank + 1] - bounds[rank]; }
+};
+
 int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energies, double *vecs,
-             double *resid, sbd_report *rep);
+             double *resid, sbd_report *rep, ShardCtx *shard = nullptr);
+// sigma of this rank's rows: the source blocks pass around the ring of ranks (shard.cu)
+void ring_sigma(ShardCtx &sh, Ctx &c, const void *x_rows, double *y_rows, sbd_precision prec, cudaStream_t s,
+                const double *x64_rows = nullptr);
 
 }  // namespace sbd

@@ -21,15 +21,23 @@
 // into the converged direction.
 //
 // The vector kernels are HBM-streaming: every thread keeps kLoad independent
-// loads in flight before it consumes them.
+// loads in flight before it consumes them.  On GB300 their FP64 multiply-adds,
+// not HBM, set the pace (the FP64 pipe is ~1/64 of the FP32 pipe), so solves
+// that take FP64-accurate arithmetic from FP32 pairs (SBD_F32X2, and mixed
+// solves refined that way) also form the dot products, axpys and Ritz
+// combinations in pairs: each stored FP64 value is split on the integer pipe,
+// products and sums run on the FP32 pipe (48-bit accurate), and each result is
+// rounded to FP64 once.
 #include <math.h>
 #include <stdio.h>
 
 #include <algorithm>
 #include <chrono>
+#include <type_traits>
 
 #include "common.cuh"
 #include "jacobi.cuh"
+#include "pair.cuh"
 
 namespace sbd {
 
@@ -64,38 +72,60 @@ __device__ __forceinline__ T block_sum(T v, T *red)
 }
 
 // partial[b*kPart + a] = sum over block b's elements of X[a][i] y[i] (a < k <= kDotMax);
-// with NORM also partial[b*kPart + kDotMax] = sum y[i]^2
-template <bool NORM, int KB>
+// with NORM also partial[b*kPart + kDotMax] = sum y[i]^2.  PAIR: each thread's products and sums
+// in FP32 pairs (48-bit accurate), converted to FP64 once per thread before the block sum.
+template <bool NORM, int KB, bool PAIR>
 __global__ void __launch_bounds__(kBlas) mdot_partial(const double *__restrict__ X, int64_t ldx, int k,
                                                       const double *__restrict__ y, int64_t N, double *partial)
 {
     __shared__ double red[kBlas / 32];
-    double acc[KB];
+    using Acc = typename std::conditional<PAIR, F2, double>::type;
+    Acc acc[KB];
 #pragma unroll
-    for (int a = 0; a < KB; ++a) acc[a] = 0.0;
-    double an = 0.0;
+    for (int a = 0; a < KB; ++a) acc[a] = Acc(0.f);
+    Acc an = Acc(0.f);
     for (int64_t i = blockIdx.x * (int64_t)kBlas + threadIdx.x; i < N; i += (int64_t)gridDim.x * kBlas) {
-        const double yi = y[i];
-        if (NORM) an += yi * yi;
+        const double yd = y[i];
+        if constexpr (PAIR) {
+            const F2 yi = f2_split(yd);
+            if (NORM) f2_mac(an, yi, yi);
 #pragma unroll
-        for (int a0 = 0; a0 < KB; a0 += kLoad) {
-            if (a0 < k) {
-                double x[kLoad];
+            for (int a0 = 0; a0 < KB; a0 += kLoad) {
+                if (a0 < k) {
+                    double x[kLoad];
 #pragma unroll
-                for (int u = 0; u < kLoad; ++u) x[u] = (a0 + u < k) ? X[(a0 + u) * ldx + i] : 0.0;
+                    for (int u = 0; u < kLoad; ++u) x[u] = (a0 + u < k) ? X[(a0 + u) * ldx + i] : 0.0;
 #pragma unroll
-                for (int u = 0; u < kLoad; ++u) acc[a0 + u] += x[u] * yi;
+                    for (int u = 0; u < kLoad; ++u)
+                        if (a0 + u < k) f2_mac(acc[a0 + u], f2_split(x[u]), yi);
+                }
+            }
+        } else {
+            if (NORM) an += yd * yd;
+#pragma unroll
+            for (int a0 = 0; a0 < KB; a0 += kLoad) {
+                if (a0 < k) {
+                    double x[kLoad];
+#pragma unroll
+                    for (int u = 0; u < kLoad; ++u) x[u] = (a0 + u < k) ? X[(a0 + u) * ldx + i] : 0.0;
+#pragma unroll
+                    for (int u = 0; u < kLoad; ++u) acc[a0 + u] += x[u] * yd;
+                }
             }
         }
     }
+    auto value = [](Acc v) -> double {
+        if constexpr (PAIR) return f2_value(v);
+        else return v;
+    };
 #pragma unroll
     for (int a = 0; a < KB; ++a)
         if (a < k) {  // k is uniform over the block
-            const double s = block_sum(acc[a], red);
+            const double s = block_sum(value(acc[a]), red);
             if (threadIdx.x == 0) partial[blockIdx.x * kPart + a] = s;
         }
     if (NORM) {
-        const double s = block_sum(an, red);
+        const double s = block_sum(value(an), red);
         if (threadIdx.x == 0) partial[blockIdx.x * kPart + kDotMax] = s;
     }
 }
@@ -118,27 +148,47 @@ __global__ void mdot_final(const double *partial, int nblocks, int k, double *ou
     }
 }
 
-// y -= sum_a coef[a] X[a] (a < k <= kMaxSub); with NORM, partial[b*kPart + kDotMax] = sum of the new y^2
-template <bool NORM>
+// y -= sum_a coef[a] X[a] (a < k <= kMaxSub); with NORM, partial[b*kPart + kDotMax] = sum of the new y^2.
+// PAIR: y and the products summed in an FP32 pair, one FP64 rounding per element.
+template <bool NORM, bool PAIR>
 __global__ void __launch_bounds__(kBlas) maxpy_kernel(const double *__restrict__ X, int64_t ldx, int k,
                                                       const double *__restrict__ coef, double *y, int64_t N,
                                                       double *partial)
 {
     __shared__ double cs[kMaxSub];
+    __shared__ F2 cs2[kMaxSub];  // -coef[a] as pairs
     __shared__ double red[kBlas / 32];
-    for (int a = threadIdx.x; a < kMaxSub; a += kBlas) cs[a] = a < k ? coef[a] : 0.0;
+    for (int a = threadIdx.x; a < kMaxSub; a += kBlas) {
+        const double c = a < k ? coef[a] : 0.0;
+        cs[a] = c;
+        if (PAIR) cs2[a] = a < k ? f2_neg(f2_split(c)) : F2(0.f);
+    }
     __syncthreads();
     double an = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)kBlas + threadIdx.x; i < N; i += (int64_t)gridDim.x * kBlas) {
-        double s = 0.0;
-        for (int a0 = 0; a0 < k; a0 += kLoad) {
-            double x[kLoad];
+        double yn;
+        if constexpr (PAIR) {
+            F2 acc = f2_split(y[i]);
+            for (int a0 = 0; a0 < k; a0 += kLoad) {
+                double x[kLoad];
 #pragma unroll
-            for (int u = 0; u < kLoad; ++u) x[u] = (a0 + u < k) ? X[(a0 + u) * ldx + i] : 0.0;
+                for (int u = 0; u < kLoad; ++u) x[u] = (a0 + u < k) ? X[(a0 + u) * ldx + i] : 0.0;
 #pragma unroll
-            for (int u = 0; u < kLoad; ++u) s += cs[min(a0 + u, kMaxSub - 1)] * x[u];
+                for (int u = 0; u < kLoad; ++u)
+                    if (a0 + u < k) f2_mac(acc, cs2[a0 + u], f2_split(x[u]));
+            }
+            yn = f2_value(acc);
+        } else {
+            double s = 0.0;
+            for (int a0 = 0; a0 < k; a0 += kLoad) {
+                double x[kLoad];
+#pragma unroll
+                for (int u = 0; u < kLoad; ++u) x[u] = (a0 + u < k) ? X[(a0 + u) * ldx + i] : 0.0;
+#pragma unroll
+                for (int u = 0; u < kLoad; ++u) s += cs[min(a0 + u, kMaxSub - 1)] * x[u];
+            }
+            yn = y[i] - s;
         }
-        const double yn = y[i] - s;
         y[i] = yn;
         if (NORM) an += yn * yn;
     }
@@ -151,7 +201,8 @@ __global__ void __launch_bounds__(kBlas) maxpy_kernel(const double *__restrict__
 // out[j] = sum_a Y[a*ldy + j] X[a] and hout[j] = sum_a Y[a*ldy + j] H[a] for j < m <= kRitzMax, a < k.
 // With RITZ (the Ritz step), also: r = hout - theta[j] out, partial[b*kPart + j] = sum r^2 and the
 // preconditioned correction tc[j] = r / (sign(d) max(|d|, delta)), d = hd - theta[j].
-template <bool RITZ, int M>
+// PAIR: the sums over a in FP32 pairs, one FP64 rounding per output element.
+template <bool RITZ, int M, bool PAIR>
 __global__ void __launch_bounds__(kBlas) combine_kernel(const double *__restrict__ X, const double *__restrict__ H,
                                                         int64_t ldx, int k, const double *__restrict__ Y, int ldy,
                                                         int m, double *out, double *hout, int64_t ldo,
@@ -162,17 +213,23 @@ __global__ void __launch_bounds__(kBlas) combine_kernel(const double *__restrict
     __shared__ double ys[kMaxSub * kRitzMax];
     __shared__ double th[kRitzMax];
     __shared__ double red[kBlas / 32];
-    for (int t = threadIdx.x; t < k * m; t += kBlas) ys[t] = Y[(t / m) * ldy + (t % m)];
+    F2 *ys2 = reinterpret_cast<F2 *>(ys);  // PAIR: the same coefficients as pairs (8 bytes each)
+    for (int t = threadIdx.x; t < k * m; t += kBlas) {
+        const double v = Y[(t / m) * ldy + (t % m)];
+        if (PAIR) ys2[t] = f2_split(v);
+        else ys[t] = v;
+    }
     if (RITZ)
         for (int j = threadIdx.x; j < m; j += kBlas) th[j] = theta[j];
     __syncthreads();
+    using Acc = typename std::conditional<PAIR, F2, double>::type;
     double racc[M];
 #pragma unroll
     for (int j = 0; j < M; ++j) racc[j] = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)kBlas + threadIdx.x; i < N; i += (int64_t)gridDim.x * kBlas) {
-        double u[M], hu[M];
+        Acc u[M], hu[M];
 #pragma unroll
-        for (int j = 0; j < M; ++j) u[j] = hu[j] = 0.0;
+        for (int j = 0; j < M; ++j) u[j] = hu[j] = Acc(0.f);
         for (int a0 = 0; a0 < k; a0 += kLoad / 2) {
             double x[kLoad / 2], h[kLoad / 2];
 #pragma unroll
@@ -184,21 +241,41 @@ __global__ void __launch_bounds__(kBlas) combine_kernel(const double *__restrict
 #pragma unroll
             for (int q = 0; q < kLoad / 2; ++q) {
                 const int a = min(a0 + q, kMaxSub - 1);
+                if constexpr (PAIR) {
+                    if (a0 + q < k) {
+                        const F2 xs = f2_split(x[q]), hs = f2_split(h[q]);
 #pragma unroll
-                for (int j = 0; j < M; ++j)
-                    if (j < m) {
-                        u[j] += ys[a * m + j] * x[q];
-                        hu[j] += ys[a * m + j] * h[q];
+                        for (int j = 0; j < M; ++j)
+                            if (j < m) {
+                                f2_mac(u[j], ys2[a * m + j], xs);
+                                f2_mac(hu[j], ys2[a * m + j], hs);
+                            }
                     }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < M; ++j)
+                        if (j < m) {
+                            u[j] += ys[a * m + j] * x[q];
+                            hu[j] += ys[a * m + j] * h[q];
+                        }
+                }
             }
         }
 #pragma unroll
         for (int j = 0; j < M; ++j)
             if (j < m) {
-                out[j * ldo + i] = u[j];
-                hout[j * ldo + i] = hu[j];
+                double uj, huj;
+                if constexpr (PAIR) {
+                    uj = f2_value(u[j]);
+                    huj = f2_value(hu[j]);
+                } else {
+                    uj = u[j];
+                    huj = hu[j];
+                }
+                out[j * ldo + i] = uj;
+                hout[j * ldo + i] = huj;
                 if (RITZ) {
-                    const double r = hu[j] - th[j] * u[j];
+                    const double r = huj - th[j] * uj;
                     racc[j] += r * r;
                     const double d = hd[i] - th[j];
                     tc[j * ldo + i] = r * precond_factor(d, delta);
@@ -345,71 +422,137 @@ __global__ void jacobi_kernel(const double *__restrict__ T, int ldt, int k, doub
 struct Work {
     Ctx &c;
     cudaStream_t s;
-    int64_t N;
+    int64_t N;      // local vector length (this rank's rows in a sharded solve)
+    int64_t off;    // global index of local element 0
+    ShardCtx *sh;   // null: one process holds the whole vectors
+    bool pair = false;  // dot products, axpys and Ritz combinations in FP32 pairs (mixed solves)
     int grid;
     double *partial = nullptr;  // [grid][kPart]
-    double *dscal = nullptr;    // device scalars
+    double *dscal = nullptr;    // kMaxSub + 1 doubles: local dot products before the sum over ranks
     double *pv = nullptr;
     int64_t *pi = nullptr;
     std::vector<double> hpart;
-    explicit Work(Ctx &cc) : c(cc), s(cc.stream), N(cc.N), grid(blas_grid(cc, cc.N)) {}
+    Work(Ctx &cc, int64_t n, int64_t o, ShardCtx *shard)
+        : c(cc), s(cc.stream), N(n), off(o), sh(shard), grid(blas_grid(cc, n)) {}
 
-    // out1[a*st1] (and out2[a*st2]) = X[a] . y for a < k; with norm2, also y . y
+    // sum over ranks of n host doubles (no-op without sharding)
+    void allreduce(double *h, int n)
+    {
+        if (!sh || sh->world == 1 || n == 0) return;
+        if (sh->comm.allreduce_sum(sh->comm.ctx, h, n) != 0) fail(SBD_ERR_CUDA, "allreduce_sum callback failed");
+    }
+    // replace n device doubles (stride st) by their sums over the ranks
+    void globalize(double *dev, int64_t st, int n)
+    {
+        if (!sh || sh->world == 1 || n == 0 || !dev) return;
+        std::vector<double> h((size_t)n);
+        SBD_CUDA(cudaMemcpy2DAsync(h.data(), sizeof(double), dev, st * sizeof(double), sizeof(double), n,
+                                   cudaMemcpyDeviceToHost, s));
+        SBD_CUDA(cudaStreamSynchronize(s));
+        allreduce(h.data(), n);
+        SBD_CUDA(cudaMemcpy2DAsync(dev, st * sizeof(double), h.data(), sizeof(double), sizeof(double), n,
+                                   cudaMemcpyHostToDevice, s));
+    }
+
+    // out1[a*st1] (and out2[a*st2]) = X[a] . y for a < k; with norm2, also y . y.  In a sharded solve
+    // the local sums go to a contiguous scratch first, are summed over the ranks, then written out
+    // (out1 and out2 may share an entry).
     void dots(const double *X, int64_t ldx, int k, const double *y, double *out1, int64_t st1,
               double *out2 = nullptr, int64_t st2 = 0, double *norm2 = nullptr)
     {
-        for (int a0 = 0; a0 < k || (a0 == 0 && norm2); a0 += kDotMax) {
-            const int kb = std::min(kDotMax, k - a0);
+        if (sh && sh->world > 1) {
+            double *tmp = dscal;  // kMaxSub + 1 doubles
+            local_dots(X, ldx, k, y, tmp, 1, nullptr, 0, norm2 ? tmp + k : nullptr);
+            std::vector<double> h((size_t)k + 1, 0.0);
+            const int n = k + (norm2 ? 1 : 0);
+            SBD_CUDA(cudaMemcpyAsync(h.data(), tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+            SBD_CUDA(cudaStreamSynchronize(s));
+            allreduce(h.data(), n);
+            if (k) {
+                SBD_CUDA(cudaMemcpy2DAsync(out1, st1 * sizeof(double), h.data(), sizeof(double), sizeof(double), k,
+                                           cudaMemcpyHostToDevice, s));
+                if (out2)
+                    SBD_CUDA(cudaMemcpy2DAsync(out2, st2 * sizeof(double), h.data(), sizeof(double), sizeof(double), k,
+                                               cudaMemcpyHostToDevice, s));
+            }
+            if (norm2) SBD_CUDA(cudaMemcpyAsync(norm2, h.data() + k, sizeof(double), cudaMemcpyHostToDevice, s));
+            SBD_CUDA(cudaStreamSynchronize(s));  // h leaves scope
+            return;
+        }
+        local_dots(X, ldx, k, y, out1, st1, out2, st2, norm2);
+    }
+    template <bool NORM, bool PAIR>
+    void launch_mdot(const double *Xa, int64_t ldx, int kb, const double *y)
+    {
+        if (kb <= 8) mdot_partial<NORM, 8, PAIR><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+        else if (PAIR || kb <= 16) mdot_partial<NORM, 16, PAIR><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+        else mdot_partial<NORM, kDotMax, false><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+        SBD_LAUNCH("mdot_partial");
+    }
+    void local_dots(const double *X, int64_t ldx, int k, const double *y, double *out1, int64_t st1,
+                    double *out2, int64_t st2, double *norm2)
+    {
+        // pair sums take twice the accumulator registers: at most 16 dot products per launch
+        const int step = pair ? 16 : kDotMax;
+        for (int a0 = 0; a0 < k || (a0 == 0 && norm2); a0 += step) {
+            const int kb = std::min(step, k - a0);
             const bool nrm = norm2 && a0 == 0;
             const double *Xa = X + a0 * ldx;
-            if (kb <= 8) {
-                if (nrm) mdot_partial<true, 8><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
-                else mdot_partial<false, 8><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
-            } else if (kb <= 16) {
-                if (nrm) mdot_partial<true, 16><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
-                else mdot_partial<false, 16><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+            if (pair) {
+                if (nrm) launch_mdot<true, true>(Xa, ldx, kb, y);
+                else launch_mdot<false, true>(Xa, ldx, kb, y);
             } else {
-                if (nrm) mdot_partial<true, kDotMax><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
-                else mdot_partial<false, kDotMax><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+                if (nrm) launch_mdot<true, false>(Xa, ldx, kb, y);
+                else launch_mdot<false, false>(Xa, ldx, kb, y);
             }
-            SBD_LAUNCH("mdot_partial");
             mdot_final<<<1, kDotMax + 1, 0, s>>>(partial, grid, kb, out1 + a0 * st1, st1,
                                                  out2 ? out2 + a0 * st2 : nullptr, st2, nrm ? norm2 : nullptr);
             SBD_LAUNCH("mdot_final");
-            if (k <= a0 + kDotMax) break;
+            if (k <= a0 + step) break;
         }
     }
     // y -= X coef; with norm2, also the new y . y
     void axpys(const double *X, int64_t ldx, int k, const double *coef, double *y, double *norm2 = nullptr)
     {
         if (norm2) {
-            maxpy_kernel<true><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
+            if (pair) maxpy_kernel<true, true><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
+            else maxpy_kernel<true, false><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
             SBD_LAUNCH("maxpy_kernel");
             mdot_final<<<1, kDotMax + 1, 0, s>>>(partial, grid, 0, nullptr, 0, nullptr, 0, norm2);
             SBD_LAUNCH("mdot_final");
+            globalize(norm2, 1, 1);
         } else {
-            maxpy_kernel<false><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
+            if (pair) maxpy_kernel<false, true><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
+            else maxpy_kernel<false, false><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
             SBD_LAUNCH("maxpy_kernel");
         }
+    }
+    template <bool RITZ, bool PAIR>
+    void launch_combine_p(const double *X, const double *H, int64_t ldx, int k, const double *Y, int ldy, int m,
+                          double *out, double *hout, int64_t ldo, const double *theta, const double *hd, double delta,
+                          double *tc)
+    {
+        if (m <= 1)
+            combine_kernel<RITZ, 1, PAIR><<<grid, kBlas, 0, s>>>(X, H, ldx, k, Y, ldy, m, out, hout, ldo, theta, hd,
+                                                                 delta, tc, partial, N);
+        else if (m <= 4)
+            combine_kernel<RITZ, 4, PAIR><<<grid, kBlas, 0, s>>>(X, H, ldx, k, Y, ldy, m, out, hout, ldo, theta, hd,
+                                                                 delta, tc, partial, N);
+        else if (m <= 8)
+            combine_kernel<RITZ, 8, PAIR><<<grid, kBlas, 0, s>>>(X, H, ldx, k, Y, ldy, m, out, hout, ldo, theta, hd,
+                                                                 delta, tc, partial, N);
+        else
+            combine_kernel<RITZ, kRitzMax, PAIR><<<grid, kBlas, 0, s>>>(X, H, ldx, k, Y, ldy, m, out, hout, ldo, theta,
+                                                                        hd, delta, tc, partial, N);
+        SBD_LAUNCH("combine_kernel");
     }
     template <bool RITZ>
     void launch_combine(const double *X, const double *H, int64_t ldx, int k, const double *Y, int ldy, int m,
                         double *out, double *hout, int64_t ldo, const double *theta, const double *hd, double delta,
                         double *tc)
     {
-        if (m <= 1)
-            combine_kernel<RITZ, 1><<<grid, kBlas, 0, s>>>(X, H, ldx, k, Y, ldy, m, out, hout, ldo, theta, hd, delta,
-                                                           tc, partial, N);
-        else if (m <= 4)
-            combine_kernel<RITZ, 4><<<grid, kBlas, 0, s>>>(X, H, ldx, k, Y, ldy, m, out, hout, ldo, theta, hd, delta,
-                                                           tc, partial, N);
-        else if (m <= 8)
-            combine_kernel<RITZ, 8><<<grid, kBlas, 0, s>>>(X, H, ldx, k, Y, ldy, m, out, hout, ldo, theta, hd, delta,
-                                                           tc, partial, N);
-        else
-            combine_kernel<RITZ, kRitzMax><<<grid, kBlas, 0, s>>>(X, H, ldx, k, Y, ldy, m, out, hout, ldo, theta, hd,
-                                                                  delta, tc, partial, N);
-        SBD_LAUNCH("combine_kernel");
+        if (pair) launch_combine_p<RITZ, true>(X, H, ldx, k, Y, ldy, m, out, hout, ldo, theta, hd, delta, tc);
+        else launch_combine_p<RITZ, false>(X, H, ldx, k, Y, ldy, m, out, hout, ldo, theta, hd, delta, tc);
     }
     // out[j] = sum_a Y[a][j] X[a], hout[j] = sum_a Y[a][j] H[a], j < m, a < k
     void combine(const double *X, const double *H, int64_t ldx, int k, const double *Y, int ldy, int m, double *out,
@@ -433,11 +576,11 @@ struct Work {
         hpart.assign((size_t)grid * kPart, 0.0);
         SBD_CUDA(cudaMemcpyAsync(hpart.data(), partial, sizeof(double) * grid * kPart, cudaMemcpyDeviceToHost, s));
         SBD_CUDA(cudaStreamSynchronize(s));
-        for (int j = 0; j < m; ++j) {
-            double acc = 0.0;
-            for (int b = 0; b < grid; ++b) acc += hpart[(size_t)b * kPart + j];
-            rn_host[j] = sqrt(acc);
-        }
+        std::vector<double> acc((size_t)m, 0.0);
+        for (int j = 0; j < m; ++j)
+            for (int b = 0; b < grid; ++b) acc[j] += hpart[(size_t)b * kPart + j];
+        allreduce(acc.data(), m);
+        for (int j = 0; j < m; ++j) rn_host[j] = sqrt(acc[j]);
     }
     // residual norms ||HU_j - theta_j U_j||, j < m (theta on device)
     void resid_norms(const double *U, const double *HU, int64_t ld, int m, const double *theta, double *out_host)
@@ -451,8 +594,12 @@ struct Work {
         scale_kernel<<<grid, kBlas, 0, s>>>(src, dst, f, N);
         SBD_LAUNCH("scale_kernel");
     }
-    int64_t argmin(const double *x, const std::vector<int64_t> &excl, int64_t *dexcl)
+    // global index of the smallest entry not in excl (global indices); ties: lowest index
+    int64_t argmin(const double *x, const std::vector<int64_t> &excl_global, int64_t *dexcl)
     {
+        std::vector<int64_t> excl;
+        for (int64_t g : excl_global)
+            if (g >= off && g < off + N) excl.push_back(g - off);
         if (!excl.empty())
             SBD_CUDA(cudaMemcpyAsync(dexcl, excl.data(), excl.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
         argmin_partial<<<grid, kBlas, 0, s>>>(x, N, dexcl, (int)excl.size(), pv, pi);
@@ -469,6 +616,33 @@ struct Work {
                 bv = v[b];
                 bi = id[b];
             }
+        if (bi >= 0) bi += off;
+        return pick_global(bv, bi, false);
+    }
+    // the rank-local candidates (value, global index) of every rank, gathered through a sum over a
+    // one-slot-per-rank array; the best by value (smallest, or largest with `largest`), ties by index
+    int64_t pick_global(double &val, int64_t idx, bool largest)
+    {
+        if (!sh || sh->world == 1) return idx;
+        const int W = sh->world;
+        std::vector<double> buf((size_t)3 * W, 0.0);
+        buf[(size_t)3 * sh->rank] = idx >= 0 ? 1.0 : 0.0;
+        buf[(size_t)3 * sh->rank + 1] = idx >= 0 ? val : 0.0;
+        buf[(size_t)3 * sh->rank + 2] = (double)idx;
+        allreduce(buf.data(), 3 * W);
+        int64_t bi = -1;
+        double bv = 0.0;
+        for (int r = 0; r < W; ++r) {
+            if (buf[(size_t)3 * r] == 0.0) continue;
+            const double v = buf[(size_t)3 * r + 1];
+            const int64_t i = (int64_t)buf[(size_t)3 * r + 2];
+            const bool better = largest ? v > bv : v < bv;
+            if (bi < 0 || better || (v == bv && i < bi)) {
+                bv = v;
+                bi = i;
+            }
+        }
+        val = bv;
         return bi;
     }
     double value_at_argmaxabs(const double *x)
@@ -488,27 +662,38 @@ struct Work {
                 bi = id[b];
             }
         double val = 0.0;
-        SBD_CUDA(cudaMemcpyAsync(&val, x + bi, sizeof(double), cudaMemcpyDeviceToHost, s));
-        SBD_CUDA(cudaStreamSynchronize(s));
-        return val;
+        if (bi >= 0) {
+            SBD_CUDA(cudaMemcpyAsync(&val, x + bi, sizeof(double), cudaMemcpyDeviceToHost, s));
+            SBD_CUDA(cudaStreamSynchronize(s));
+        }
+        if (!sh || sh->world == 1) return val;
+        // the signed value at the largest |x| over all ranks
+        double a = fabs(val);
+        const int64_t g = pick_global(a, bi >= 0 ? bi + off : -1, true);
+        std::vector<double> h(1, (bi >= 0 && bi + off == g) ? val : 0.0);
+        allreduce(h.data(), 1);
+        return h[0];
     }
 };
 
 }  // namespace
 
 int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energies, double *vecs, double *resid,
-             sbd_report *rep)
+             sbd_report *rep, ShardCtx *shard)
 {
     using clock = std::chrono::steady_clock;
     const auto t_start = clock::now();
-    const int64_t N = c.N;
-    if (nroots < 1 || nroots > kRitzMax || nroots > N) fail(SBD_ERR_INVALID_ARG, "nroots must be in 1..min(16, N)");
+    // a sharded solve holds only this rank's rows of every vector
+    const int64_t N = shard ? shard->rows() * c.nB : c.N;
+    const int64_t off = shard ? shard->row0() * c.nB : 0;
+    const double *hd = c.hd + off;
+    if (nroots < 1 || nroots > kRitzMax || nroots > c.N) fail(SBD_ERR_INVALID_ARG, "nroots must be in 1..min(16, N)");
     if (!(tol > 0.0)) fail(SBD_ERR_INVALID_ARG, "tol must be positive");
     const double delta = c.opt.delta > 0.0 ? c.opt.delta : 1e-4;
     const int max_iter = c.opt.max_iter > 0 ? c.opt.max_iter : 200;
     int max_sub = c.opt.max_subspace > 0 ? c.opt.max_subspace : std::max(24, 8 * nroots);
-    max_sub = (int)std::min<int64_t>(std::min(max_sub, kMaxSub), N);
-    if (max_sub < 2 * nroots && N >= 2 * nroots) max_sub = 2 * nroots;
+    max_sub = (int)std::min<int64_t>(std::min(max_sub, kMaxSub), c.N);
+    if (max_sub < 2 * nroots && c.N >= 2 * nroots) max_sub = 2 * nroots;
     const bool mixed = prec == SBD_MIXED;
     // the FP64-accurate sigma: the solve's own precision, or for mixed solves the refinement precision
     const sbd_precision exact_prec =
@@ -535,7 +720,8 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
     SBD_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(2 * sizeof(double) * kMaxSub * kMaxSub)));
 
-    Work w(c);
+    Work w(c, N, off, shard);
+    w.pair = prec == SBD_F32X2 || (mixed && exact_prec == SBD_F32X2);
     std::vector<void *> owned;
     auto grab = [&](size_t bytes) {
         void *p = dalloc(c, bytes);
@@ -560,6 +746,7 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
         w.partial = (double *)grab(sizeof(double) * (size_t)w.grid * kPart);
         w.pv = (double *)grab(sizeof(double) * w.grid);
         w.pi = (int64_t *)grab(sizeof(int64_t) * w.grid);
+        w.dscal = (double *)grab(sizeof(double) * (kMaxSub + 1));
         const int64_t ld = N;
         SBD_CUDA(cudaEventCreate(&ev0));
         SBD_CUDA(cudaEventCreate(&ev1));
@@ -572,10 +759,12 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
             for (int b = b0; b < b0 + nb; ++b) {
                 if (!fp64) {
                     to_float(V + b * ld, c32, N, w.s);
-                    sigma_apply(c, c32, W + b * ld, SBD_MIXED, w.s, V + b * ld);
+                    if (shard) ring_sigma(*shard, c, c32, W + b * ld, SBD_MIXED, w.s, V + b * ld);
+                    else sigma_apply(c, c32, W + b * ld, SBD_MIXED, w.s, V + b * ld);
                     r.sigma_mixed++;
                 } else {
-                    sigma_apply(c, V + b * ld, W + b * ld, exact_prec, w.s);
+                    if (shard) ring_sigma(*shard, c, V + b * ld, W + b * ld, exact_prec, w.s);
+                    else sigma_apply(c, V + b * ld, W + b * ld, exact_prec, w.s);
                     r.sigma_fp64++;
                 }
                 exact[b] = fp64;
@@ -614,10 +803,12 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
         SBD_CUDA(cudaMemsetAsync(V, 0, (size_t)nroots * N * sizeof(double), w.s));
         std::vector<int64_t> chosen;
         for (int j = 0; j < nroots; ++j) {
-            const int64_t idx = w.argmin(c.hd, chosen, dexcl);
+            const int64_t idx = w.argmin(hd, chosen, dexcl);  // global index
             chosen.push_back(idx);
-            set_kernel<<<1, 1, 0, w.s>>>(V + j * ld, idx, 1.0);
-            SBD_LAUNCH("set_kernel");
+            if (idx >= off && idx < off + N) {
+                set_kernel<<<1, 1, 0, w.s>>>(V + j * ld, idx - off, 1.0);
+                SBD_LAUNCH("set_kernel");
+            }
         }
         int k = nroots;
         sigma_cols(0, k, !mixed);
@@ -633,7 +824,7 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
             jacobi_kernel<<<1, 256, 2 * sizeof(double) * k * k, w.s>>>(T, kMaxSub, k, theta, Y, kMaxSub);
             SBD_LAUNCH("jacobi_kernel");
             // 2d + 2f. Ritz vectors, residual norms and the preconditioned corrections in one pass
-            w.ritz(V, W, ld, k, Y, kMaxSub, nroots, U, HU, theta, c.hd, delta, TC, rn.data());
+            w.ritz(V, W, ld, k, Y, kMaxSub, nroots, U, HU, theta, hd, delta, TC, rn.data());
             SBD_CUDA(cudaMemcpyAsync(th.data(), theta, sizeof(double) * k, cudaMemcpyDeviceToHost, w.s));
             SBD_CUDA(cudaStreamSynchronize(w.s));
             harvest_timing(c);
@@ -668,7 +859,7 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
                     SBD_CUDA(cudaMemcpyAsync(theta, th.data(), sizeof(double) * nroots, cudaMemcpyHostToDevice, w.s));
                     w.resid_norms(U, HU, ld, nroots, theta, rn.data());
                     for (int j = 0; j < nroots; ++j) {
-                        precond_kernel<<<w.grid, kBlas, 0, w.s>>>(U + j * ld, HU + j * ld, c.hd, theta + j, delta,
+                        precond_kernel<<<w.grid, kBlas, 0, w.s>>>(U + j * ld, HU + j * ld, hd, theta + j, delta,
                                                                   TC + j * ld, N);
                         SBD_LAUNCH("precond_kernel");
                     }

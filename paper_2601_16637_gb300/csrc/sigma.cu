@@ -36,6 +36,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "pair.cuh"
 
 namespace sbd {
 
@@ -43,62 +44,6 @@ namespace {
 
 constexpr int kGroup = 8;  // lanes cooperating on one output column
 constexpr int kGroupsPerWarp = 32 / kGroup;
-
-// A value hi + lo of two floats (|lo| <= ulp(hi)/2 after renormalisation).
-struct F2 {
-    float hi, lo;
-    F2() = default;
-    __host__ __device__ constexpr F2(float h) : hi(h), lo(0.f) {}
-    __host__ __device__ constexpr F2(float h, float l) : hi(h), lo(l) {}
-};
-
-// x = hi + lo to 48 bits.  Done on the integer pipe: hi keeps the sign, the exponent and the top 23
-// mantissa bits of x (truncation), lo is the value of the 29 bits cut off; only |x| outside the FP32
-// normal range takes the FP64 route (FP64 conversions and subtraction run on the FP64 pipe, which on
-// this GPU is ~1/64 of the FP32 rate and would otherwise dominate the staging of pair amplitudes).
-__device__ __forceinline__ F2 f2_split(double x)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned int h = (unsigned int)(b >> 32), l = (unsigned int)b;
-    const int e = (int)((h >> 20) & 0x7FFu);  // biased FP64 exponent
-    if (e < 1023 - 126 || e > 1023 + 127) {
-        const float hi = __double2float_rn(x);
-        return F2(hi, __double2float_rn(x - (double)hi));
-    }
-    const unsigned int sign = h & 0x80000000u;
-    const float hi = __uint_as_float(sign | ((unsigned int)(e - 1023 + 127) << 23) | ((h & 0xFFFFFu) << 3) | (l >> 29));
-    const float lo = ldexpf(__uint2float_rn(l & 0x1FFFFFFFu), e - 1023 - 52);
-    return F2(hi, sign ? -lo : lo);
-}
-__device__ __forceinline__ double f2_value(F2 a) { return (double)a.hi + (double)a.lo; }
-
-// acc += a * b.  The product's high part is exact to 48 bits (hi*hi and its rounding error from
-// a fused multiply-add, plus the cross terms); it enters acc.hi through a two-sum whose error
-// joins the low parts, which are gathered in acc.lo and renormalised by f2_add.  The explicit
-// _rn intrinsics keep the compiler from fusing the two-sum into multiply-adds.
-__device__ __forceinline__ void f2_mac(F2 &acc, F2 a, F2 b)
-{
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
-    const float s = __fadd_rn(acc.hi, p);
-    const float bb = __fsub_rn(s, acc.hi);
-    const float t = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    acc.hi = s;
-    acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, e));
-}
-
-// a + b: two-sum of the high parts, low parts added, renormalised
-__device__ __forceinline__ F2 f2_add(F2 a, F2 b)
-{
-    const float s = __fadd_rn(a.hi, b.hi);
-    const float bb = __fsub_rn(s, a.hi);
-    float t = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
-    t = __fadd_rn(t, __fadd_rn(a.lo, b.lo));
-    const float hi = __fadd_rn(s, t);
-    return F2(hi, __fsub_rn(t, __fsub_rn(hi, s)));
-}
 
 template <typename T>
 constexpr bool kIsF2 = std::is_same<T, F2>::value;
@@ -1129,7 +1074,7 @@ namespace {
 
 // The three passes of one source block for the output rows of a plan (see BlockPlan).
 template <typename T>
-void apply_block(BlockPlan &p, const typename In<T>::type *Cb, double *S, cudaStream_t s)
+void apply_block(BlockPlan &p, const typename In<T>::type *Cb, double *S, cudaStream_t s, const double *x64)
 {
     using E = typename In<T>::type;
     Ctx &c = *p.c;
@@ -1152,7 +1097,7 @@ void apply_block(BlockPlan &p, const typename In<T>::type *Cb, double *S, cudaSt
         b.Y = S + (lo - p.r0) * c.nB;
         b.accumulate = 1;
         b.hd = c.hd + lo * c.nB;
-        b.xd64 = nullptr;
+        b.xd64 = x64 ? x64 + (lo - p.r0) * c.nB : nullptr;
         b.row_strings = ta.strings + lo;
         launch_row<T>(b, choose(c.nB, n2, sizeof(T), rmax, lim), s);
     }
@@ -1183,11 +1128,12 @@ void apply_block(BlockPlan &p, const typename In<T>::type *Cb, double *S, cudaSt
 
 }  // namespace
 
-void sigma_block_apply(BlockPlan &p, const void *cblock, double *sigma_rows, sbd_precision prec, cudaStream_t s)
+void sigma_block_apply(BlockPlan &p, const void *cblock, double *sigma_rows, sbd_precision prec, cudaStream_t s,
+                       const double *x64_rows)
 {
-    if (prec == SBD_FP64) apply_block<double>(p, static_cast<const double *>(cblock), sigma_rows, s);
-    else if (prec == SBD_F32X2) apply_block<F2>(p, static_cast<const double *>(cblock), sigma_rows, s);
-    else apply_block<float>(p, static_cast<const float *>(cblock), sigma_rows, s);
+    if (prec == SBD_FP64) apply_block<double>(p, static_cast<const double *>(cblock), sigma_rows, s, nullptr);
+    else if (prec == SBD_F32X2) apply_block<F2>(p, static_cast<const double *>(cblock), sigma_rows, s, nullptr);
+    else apply_block<float>(p, static_cast<const float *>(cblock), sigma_rows, s, x64_rows);
 }
 
 void sigma_apply(Ctx &c, const void *cvec, double *svec, sbd_precision prec, cudaStream_t s, const double *c64)

@@ -369,8 +369,10 @@ __device__ __forceinline__ int slot_of(int q, int Lp)
 
 // Singles lists, where the gathers read two tables: staged amplitudes by target j and coefficient
 // rows by key = 2*code + neg (16-byte rows, bank group = index mod 8).  Each phase of m positions is
-// filled greedily: first entries whose target and key residues are both new to the phase, then
-// entries with one new residue, then any.  Lists longer than kJointMax keep the target-only order.
+// filled one entry at a time with the untaken entry that scores highest: residues new to the phase
+// first (both sides, then one), and among those the residues most frequent among the untaken
+// entries, since the busiest residue classes bound the number of conflict-free phases.  Lists longer
+// than kJointMax keep the target-only order.
 constexpr int kJointMax = 1024;
 __device__ bool joint_order(int64_t b, int64_t e, int64_t sb, int Lp, const int32_t *__restrict__ j_src,
                             const uint32_t *__restrict__ pk, int64_t *perm)
@@ -379,26 +381,41 @@ __device__ bool joint_order(int64_t b, int64_t e, int64_t sb, int Lp, const int3
     if (L > kJointMax) return false;
     uint32_t taken[kJointMax / 32];
     for (int w = 0; w < (L + 31) / 32; ++w) taken[w] = 0u;
+    int cj[kBankGroups] = {0, 0, 0, 0, 0, 0, 0, 0}, ck[kBankGroups] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int x = 0; x < L; ++x) {
+        ++cj[j_src[b + x] & (kBankGroups - 1)];
+        ++ck[(pk[b + x] >> kPackKeyShift) & (kBankGroups - 1)];
+    }
     int q = 0;
     while (q < L) {
         const int chunk = q / 32;
         const int m = min(32, Lp - chunk * 32) / 4;
-        const int phase_end = min(L, q + m - (q - chunk * 32) % m);  // end of the phase q lies in
-        unsigned int usedJ = 0u, usedK = 0u;
-        for (int pass = 0; pass < 3 && q < phase_end; ++pass)
-            for (int x = 0; x < L && q < phase_end; ++x) {
+        const int nominal_end = q + m - (q - chunk * 32) % m;  // end of the phase q lies in
+        const int phase_end = min(L, nominal_end);
+        // padding slots (zero entries: target 0, key 0) in this phase already take residue 0 on both sides
+        unsigned int usedJ = nominal_end > L ? 1u : 0u, usedK = usedJ;
+        for (; q < phase_end; ++q) {
+            int best = -1, best_score = -1, brj = 0, brk = 0;
+            for (int x = 0; x < L; ++x) {
                 if (taken[x >> 5] >> (x & 31) & 1u) continue;
-                const unsigned int bj = 1u << (j_src[b + x] & (kBankGroups - 1));
-                const unsigned int bk = 1u << ((pk[b + x] >> kPackKeyShift) & (kBankGroups - 1));
-                const bool ok = pass == 0 ? !(usedJ & bj) && !(usedK & bk)
-                                          : (pass == 1 ? (!(usedJ & bj) || !(usedK & bk)) : true);
-                if (!ok) continue;
-                taken[x >> 5] |= 1u << (x & 31);
-                usedJ |= bj;
-                usedK |= bk;
-                perm[sb + slot_of(q, Lp)] = b + x;
-                ++q;
+                const int rj = j_src[b + x] & (kBankGroups - 1);
+                const int rk = (pk[b + x] >> kPackKeyShift) & (kBankGroups - 1);
+                const int fresh = (int)!((usedJ >> rj) & 1u) + (int)!((usedK >> rk) & 1u);
+                const int score = fresh * 4096 + cj[rj] + ck[rk];
+                if (score > best_score) {
+                    best_score = score;
+                    best = x;
+                    brj = rj;
+                    brk = rk;
+                }
             }
+            taken[best >> 5] |= 1u << (best & 31);
+            usedJ |= 1u << brj;
+            usedK |= 1u << brk;
+            --cj[brj];
+            --ck[brk];
+            perm[sb + slot_of(q, Lp)] = b + best;
+        }
     }
     return true;
 }

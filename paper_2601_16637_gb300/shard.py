@@ -95,3 +95,123 @@ def device_block_sigma(handle, bounds: Sequence[int], rank: int, precision, stre
         plans.clear()
 
     return block_sigma, close
+
+
+# ---------------------------------------------------------------------------
+# communicators for sbd_davidson_sharded
+
+
+class _DevBytes:
+    """A raw device pointer seen as a uint8 array through the CUDA array interface (for torch)."""
+
+    def __init__(self, ptr: int, nbytes: int):
+        self.__cuda_array_interface__ = {"shape": (int(nbytes),), "typestr": "|u1", "data": (int(ptr), False),
+                                         "version": 2}
+
+
+def device_view(ptr: int, nbytes: int):
+    import torch
+
+    return torch.as_tensor(_DevBytes(ptr, nbytes), device="cuda")
+
+
+class ThreadRing:
+    """Communicator for `world` ranks run as threads of one process on one device: sums in rank
+    order (so every rank sees the same bits) and ring exchanges as device-to-device copies.  Each
+    rank's thread calls `comm(rank)` once and passes the result to sbd_davidson_sharded."""
+
+    def __init__(self, world: int, timeout: float = 300.0):
+        import threading
+
+        self.world = world
+        self.barrier = threading.Barrier(world, timeout=timeout)
+        self.slots = [None] * world
+        self._keep = []
+
+    def comm(self, rank: int):
+        from . import binding as B
+
+        def allreduce(ctx, buf, n):
+            try:
+                import numpy as np
+
+                self.slots[rank] = np.ctypeslib.as_array(buf, shape=(n,)).copy()
+                self.barrier.wait()
+                total = self.slots[0].copy()
+                for r in range(1, self.world):
+                    total = total + self.slots[r]
+                self.barrier.wait()
+                np.ctypeslib.as_array(buf, shape=(n,))[:] = total
+                return 0
+            except Exception:
+                self.barrier.abort()
+                return 1
+
+        def ring(ctx, send, send_bytes, recv, recv_bytes, stream):
+            try:
+                import torch
+
+                self.slots[rank] = (int(send or 0), int(send_bytes))
+                self.barrier.wait()
+                src, nb = self.slots[(rank - 1) % self.world]
+                if nb != recv_bytes:
+                    raise ValueError("ring exchange sizes disagree")
+                device_view(recv, recv_bytes).copy_(device_view(src, nb))
+                torch.cuda.synchronize()
+                self.barrier.wait()
+                return 0
+            except Exception:
+                self.barrier.abort()
+                return 1
+
+        a, r = B.ALLREDUCE_FN(allreduce), B.RING_FN(ring)
+        self._keep += [a, r]
+        return B.sbd_comm(rank, self.world, None, a, r)
+
+
+class DistRing:
+    """Communicator over a torch.distributed process group (one process per GPU): allreduce of
+    host doubles through a tensor of the group's device, ring exchange with isend/irecv of device
+    buffers (NCCL)."""
+
+    def __init__(self, group=None):
+        import torch.distributed as dist
+
+        self.group = group
+        self.rank = dist.get_rank(group)
+        self.world = dist.get_world_size(group)
+        self._keep = []
+
+    def comm(self):
+        import numpy as np
+        import torch
+        import torch.distributed as dist
+
+        from . import binding as B
+
+        dev = "cuda" if dist.get_backend(self.group) == "nccl" else "cpu"
+
+        def allreduce(ctx, buf, n):
+            try:
+                h = np.ctypeslib.as_array(buf, shape=(n,))
+                t = torch.from_numpy(h.copy()).to(dev)
+                dist.all_reduce(t, group=self.group)
+                h[:] = t.cpu().numpy()
+                return 0
+            except Exception:
+                return 1
+
+        def ring(ctx, send, send_bytes, recv, recv_bytes, stream):
+            try:
+                reqs = [dist.isend(device_view(send, send_bytes), (self.rank + 1) % self.world, group=self.group),
+                        dist.irecv(device_view(recv, recv_bytes), (self.rank - 1) % self.world, group=self.group)]
+                for q in reqs:
+                    q.wait()
+                torch.cuda.synchronize()
+                return 0
+            except Exception:
+                return 1
+
+        a, r = B.ALLREDUCE_FN(allreduce), B.RING_FN(ring)
+        self._keep += [a, r]
+        return B.sbd_comm(self.rank, self.world, None, a, r)

@@ -239,6 +239,26 @@ def test_sigma_zero_and_full_shells(torch, B, oracle_mod):
                 assert rel_maxnorm(got, o.sigma(x)[0]) <= SIGMA_FP64_RTOL, prec
 
 
+def test_h2_minimal_basis_golden(torch, B, oracle_mod):
+    # the textbook minimal-basis H2 full CI (tests/golden): two orbitals, four determinants
+    from test_oracle_pins import load_h2_golden
+
+    vals, h, eri = load_h2_golden()
+    A = np.array([1, 2], dtype=np.uint64)
+    o = oracle_mod.Oracle(2, 1, 1, h, eri, A, A)
+    e_dense = np.linalg.eigvalsh(o.dense())[0]
+    with B.SBD(2, 1, 1, h, eri, A, A) as g:
+        x = W.random_vector(g.N, 3)
+        for prec in ("fp64", "f32x2"):
+            got = g.sigma(torch.from_numpy(x[0]).cuda(), prec).cpu().numpy()
+            assert rel_maxnorm(got, o.sigma(x)[0]) <= SIGMA_FP64_RTOL, prec
+        res = g.davidson(nroots=1, tol=1e-10, precision="fp64")
+        assert res.status == 0
+        assert abs(res.energies[0] - e_dense) <= 1e-12
+        assert abs(res.energies[0] + 1.0 / vals["R_bohr"] - vals["E_total_fci"]) <= 1.5e-4
+    o.close()
+
+
 def test_sigma_norb_64(torch, B, oracle_mod):
     # the largest orbital count: strings using bit 63
     norb, n = 64, 2

@@ -91,3 +91,51 @@ def test_ring_driver_on_one_rank_and_plan_errors(torch, B):
         for r0, r1, j0, j1 in [(5, 5, 0, 3), (0, g.nA + 1, 0, 3), (0, 3, -1, 2), (0, 3, 2, 1)]:
             with pytest.raises(B.SbdError):
                 B.sbd_block_plan_create(g.handle, r0, r1, j0, j1)
+
+
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_sharded_davidson_matches_the_single_solve(torch, B, world, prec):
+    # ranks emulated as threads on one GPU; every host decision uses the summed (global) values,
+    # so all ranks must report identical energies, and the solve must match the single-handle one
+    import threading
+
+    wl = medium()
+    tol = 1e-8 if prec == "fp64" else 1e-7
+    with B.SBD.from_workload(wl) as g:
+        ref = g.davidson(nroots=2, tol=tol, precision=prec)
+        assert ref.status == 0
+        vref = ref.vectors.cpu().numpy()
+        nA, nB = g.nA, g.nB
+    bounds = shard.row_blocks(nA, world)
+    ring = shard.ThreadRing(world, timeout=300)
+    out = [None] * world
+
+    def rank(r):
+        try:
+            with B.SBD.from_workload(wl) as h:
+                rows = (bounds[r + 1] - bounds[r]) * nB
+                e = np.empty(2)
+                res = np.empty(2)
+                v = torch.empty((2, rows), dtype=torch.float64, device="cuda")
+                rc, rep = B.sbd_davidson_sharded(h.handle, bounds, ring.comm(r), 2, tol, prec, e, v, res)
+                torch.cuda.synchronize()
+                out[r] = (rc, e, res, v.cpu().numpy(), rep.as_dict())
+        except Exception as ex:  # reported below
+            out[r] = ex
+
+    ts = [threading.Thread(target=rank, args=(r,)) for r in range(world)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join(timeout=600)
+    for o in out:
+        assert not isinstance(o, Exception) and o is not None, o
+    e0 = out[0][1]
+    for rc, e, res, v, rep in out:
+        assert rc == 0 and np.array_equal(e, e0) and np.all(res <= tol)
+    assert np.abs(e0 - ref.energies).max() <= (1e-8 if prec == "fp64" else 1e-6)
+    vfull = np.concatenate([o[3] for o in out], axis=1)
+    for j in range(2):
+        assert abs(abs(float(vfull[j] @ vref[j])) - 1.0) <= 1e-6
+        assert vfull[j][np.argmax(np.abs(vfull[j]))] > 0

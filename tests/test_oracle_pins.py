@@ -300,3 +300,58 @@ def test_pins_pass_on_the_real_oracle(oracle_mod):
 def test_planted_mistake_is_caught(oracle_mod, mutation):
     oracle_mod.build(mutation)
     assert not _pins_pass(oracle_mod, mutation), _MUTATIONS[mutation]
+
+
+# ---------------------------------------------------------------------------
+# a published worked example
+
+
+def load_h2_golden():
+    """The minimal-basis H2 full CI of the golden fixture: integrals expanded to all index
+    permutations of real orbitals, (pq|rs) = (qp|rs) = (pq|sr) = (rs|pq), and the printed values."""
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "h2_minimal_basis.txt")
+    vals, h, eri = {}, None, None
+    for line in open(path):
+        f = line.split("#")[0].split()
+        if not f:
+            continue
+        if f[0] == "h":
+            h[int(f[1]), int(f[2])] = h[int(f[2]), int(f[1])] = float(f[3])
+        elif f[0] == "eri":
+            p, q, r, s = map(int, f[1:5])
+            for a, b, c, d in [(p, q, r, s), (q, p, r, s), (p, q, s, r), (q, p, s, r)]:
+                eri[a, b, c, d] = eri[c, d, a, b] = float(f[5])
+        else:
+            vals[f[0]] = float(f[1])
+            if f[0] == "norb":
+                n = int(vals["norb"])
+                h, eri = np.zeros((n, n)), np.zeros((n, n, n, n))
+    return vals, h, eri
+
+
+def _h2_pin_passes(oracle_mod, mutation=0):
+    # the full space of one alpha and one beta electron in two orbitals: the Hartree-Fock
+    # determinant, two singles (decoupled by g/u symmetry) and the double excitation
+    vals, h, eri = load_h2_golden()
+    A = np.array([1, 2], dtype=np.uint64)
+    H = oracle_mod.Oracle(2, 1, 1, h, eri, A, A, mutation=mutation).dense()
+    hf, dbl = 0, 3  # (alpha, beta) = (orbital 0, orbital 0) and (1, 1)
+    e0 = np.linalg.eigvalsh(H)[0]
+    return bool(abs(H[hf, hf] - vals["E_hf_electronic"]) <= 1e-12  # 2 h11 + J11, exact in the printed digits
+                and abs(H[hf, dbl] - vals["coupling_hf_double"]) <= 1e-12  # K12
+                and abs(H[hf, 1]) <= 1e-15 and abs(H[hf, 2]) <= 1e-15  # Brillouin / symmetry
+                # printed to four decimals from integrals rounded to four decimals
+                and abs((e0 - H[hf, hf]) - vals["E_corr"]) <= 1.5e-4
+                and abs(e0 + 1.0 / vals["R_bohr"] - vals["E_total_fci"]) <= 1.5e-4)
+
+
+def test_h2_minimal_basis_full_ci_against_the_textbook(oracle_mod):
+    assert _h2_pin_passes(oracle_mod)
+
+
+@pytest.mark.parametrize("mutation", [1, 3, 5])
+def test_h2_pin_catches_planted_mistakes(oracle_mod, mutation):
+    oracle_mod.build(mutation)
+    assert not _h2_pin_passes(oracle_mod, mutation), _MUTATIONS[mutation]

@@ -89,3 +89,31 @@ def test_ring_sigma_over_gloo_ranks(world, oracle_mod):
     for rank, err, blocks in res:
         assert err <= 1e-13
         assert blocks == shard.ring_schedule(rank, world)
+
+
+def test_thread_ring_allreduce_is_identical_on_every_rank():
+    # the host side of the in-process communicator: sums in rank order, the same bits everywhere
+    import ctypes
+    import threading
+
+    from paper_2601_16637_gb300 import binding as B  # noqa: F401  (callback types)
+
+    world = 3
+    ring = shard.ThreadRing(world, timeout=30)
+    vals = [np.array([1e16, 1.0, -1e16 + r, 0.1 * r]) for r in range(world)]
+    got = [None] * world
+
+    def run(r):
+        c = ring.comm(r)
+        buf = (ctypes.c_double * 4)(*vals[r])
+        assert c.allreduce_sum(None, buf, 4) == 0
+        got[r] = np.array(buf[:])
+
+    ts = [threading.Thread(target=run, args=(r,)) for r in range(world)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join(timeout=60)
+    expect = vals[0] + vals[1] + vals[2]
+    for g in got:
+        assert np.array_equal(g, got[0]) and np.array_equal(g, expect)
