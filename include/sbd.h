@@ -92,8 +92,8 @@ typedef struct {
     double tol_energy;       /* > 0: a root also needs |theta_k - theta_(k-1)| <= tol_energy between
                                 consecutive iterations to count as converged (default 0: off) */
     int refine_precision;    /* FP64-accurate arithmetic of SBD_MIXED solves: SBD_F32X2 (default; the
-                                defect-correction sigma and the vector dot products, axpys and Ritz
-                                combinations in FP32 pairs) or SBD_FP64 (both on the FP64 pipe) */
+                                defect-correction sigma and the Ritz-vector combinations in FP32
+                                pairs) or SBD_FP64 (both on the FP64 pipe) */
     int restart_keep;        /* Ritz vectors a thick restart keeps; 0 = max(nroots, min(max_subspace -
                                 nroots, max(2 nroots, max_subspace/3))) */
 } sbd_options;
@@ -206,8 +206,8 @@ int sbd_sigma(sbd_handle handle, const void *c_dev, double *sigma_dev, int nvec,
  *               with FP64-accurate defect correction (sbd_options.refine_precision;
  *               the converged residual is always FP64-accurate).  Vectors, the projected
  *               eigenproblem, residuals and energies stay FP64; with SBD_F32X2 (the whole
- *               solve, or refine_precision of a mixed one) the vector kernels compute their
- *               sums in FP32 pairs (48-bit products, one FP64 rounding per stored value)
+ *               solve, or refine_precision of a mixed one) the Ritz-vector combinations sum
+ *               in FP32 pairs (48-bit products, one FP64 rounding per stored value)
  *   energies_host  nroots doubles (ascending), ecore included
  *   vecs        NULL, or host or device pointer for [nroots][nA*nB] doubles
  *   residuals_host NULL or nroots doubles

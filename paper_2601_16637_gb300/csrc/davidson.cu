@@ -22,12 +22,14 @@
 //
 // The vector kernels are HBM-streaming: every thread keeps kLoad independent
 // loads in flight before it consumes them.  On GB300 their FP64 multiply-adds,
-// not HBM, set the pace (the FP64 pipe is ~1/64 of the FP32 pipe), so solves
-// that take FP64-accurate arithmetic from FP32 pairs (SBD_F32X2, and mixed
-// solves refined that way) also form the dot products, axpys and Ritz
-// combinations in pairs: each stored FP64 value is split on the integer pipe,
-// products and sums run on the FP32 pipe (48-bit accurate), and each result is
-// rounded to FP64 once.
+// not HBM, set the pace (the FP64 pipe is ~1/64 of the FP32 pipe).  Solves that
+// take FP64-accurate arithmetic from FP32 pairs (SBD_F32X2, and mixed solves
+// refined that way) therefore form the Ritz combinations in pairs: each loaded
+// FP64 value is split once on the integer pipe and feeds one pair product per
+// combined vector on the FP32 pipe (48-bit accurate), and each result is
+// rounded to FP64 once.  Dot products and axpys use each loaded value in a
+// single product, where the split costs more than the FP64 multiply-add it
+// replaces, so they stay on the FP64 pipe.
 #include <math.h>
 #include <stdio.h>
 
@@ -72,60 +74,38 @@ __device__ __forceinline__ T block_sum(T v, T *red)
 }
 
 // partial[b*kPart + a] = sum over block b's elements of X[a][i] y[i] (a < k <= kDotMax);
-// with NORM also partial[b*kPart + kDotMax] = sum y[i]^2.  PAIR: each thread's products and sums
-// in FP32 pairs (48-bit accurate), converted to FP64 once per thread before the block sum.
-template <bool NORM, int KB, bool PAIR>
+// with NORM also partial[b*kPart + kDotMax] = sum y[i]^2
+template <bool NORM, int KB>
 __global__ void __launch_bounds__(kBlas) mdot_partial(const double *__restrict__ X, int64_t ldx, int k,
                                                       const double *__restrict__ y, int64_t N, double *partial)
 {
     __shared__ double red[kBlas / 32];
-    using Acc = typename std::conditional<PAIR, F2, double>::type;
-    Acc acc[KB];
+    double acc[KB];
 #pragma unroll
-    for (int a = 0; a < KB; ++a) acc[a] = Acc(0.f);
-    Acc an = Acc(0.f);
+    for (int a = 0; a < KB; ++a) acc[a] = 0.0;
+    double an = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)kBlas + threadIdx.x; i < N; i += (int64_t)gridDim.x * kBlas) {
-        const double yd = y[i];
-        if constexpr (PAIR) {
-            const F2 yi = f2_split(yd);
-            if (NORM) f2_mac(an, yi, yi);
+        const double yi = y[i];
+        if (NORM) an += yi * yi;
 #pragma unroll
-            for (int a0 = 0; a0 < KB; a0 += kLoad) {
-                if (a0 < k) {
-                    double x[kLoad];
+        for (int a0 = 0; a0 < KB; a0 += kLoad) {
+            if (a0 < k) {
+                double x[kLoad];
 #pragma unroll
-                    for (int u = 0; u < kLoad; ++u) x[u] = (a0 + u < k) ? X[(a0 + u) * ldx + i] : 0.0;
+                for (int u = 0; u < kLoad; ++u) x[u] = (a0 + u < k) ? X[(a0 + u) * ldx + i] : 0.0;
 #pragma unroll
-                    for (int u = 0; u < kLoad; ++u)
-                        if (a0 + u < k) f2_mac(acc[a0 + u], f2_split(x[u]), yi);
-                }
-            }
-        } else {
-            if (NORM) an += yd * yd;
-#pragma unroll
-            for (int a0 = 0; a0 < KB; a0 += kLoad) {
-                if (a0 < k) {
-                    double x[kLoad];
-#pragma unroll
-                    for (int u = 0; u < kLoad; ++u) x[u] = (a0 + u < k) ? X[(a0 + u) * ldx + i] : 0.0;
-#pragma unroll
-                    for (int u = 0; u < kLoad; ++u) acc[a0 + u] += x[u] * yd;
-                }
+                for (int u = 0; u < kLoad; ++u) acc[a0 + u] += x[u] * yi;
             }
         }
     }
-    auto value = [](Acc v) -> double {
-        if constexpr (PAIR) return f2_value(v);
-        else return v;
-    };
 #pragma unroll
     for (int a = 0; a < KB; ++a)
         if (a < k) {  // k is uniform over the block
-            const double s = block_sum(value(acc[a]), red);
+            const double s = block_sum(acc[a], red);
             if (threadIdx.x == 0) partial[blockIdx.x * kPart + a] = s;
         }
     if (NORM) {
-        const double s = block_sum(value(an), red);
+        const double s = block_sum(an, red);
         if (threadIdx.x == 0) partial[blockIdx.x * kPart + kDotMax] = s;
     }
 }
@@ -148,47 +128,27 @@ __global__ void mdot_final(const double *partial, int nblocks, int k, double *ou
     }
 }
 
-// y -= sum_a coef[a] X[a] (a < k <= kMaxSub); with NORM, partial[b*kPart + kDotMax] = sum of the new y^2.
-// PAIR: y and the products summed in an FP32 pair, one FP64 rounding per element.
-template <bool NORM, bool PAIR>
+// y -= sum_a coef[a] X[a] (a < k <= kMaxSub); with NORM, partial[b*kPart + kDotMax] = sum of the new y^2
+template <bool NORM>
 __global__ void __launch_bounds__(kBlas) maxpy_kernel(const double *__restrict__ X, int64_t ldx, int k,
                                                       const double *__restrict__ coef, double *y, int64_t N,
                                                       double *partial)
 {
     __shared__ double cs[kMaxSub];
-    __shared__ F2 cs2[kMaxSub];  // -coef[a] as pairs
     __shared__ double red[kBlas / 32];
-    for (int a = threadIdx.x; a < kMaxSub; a += kBlas) {
-        const double c = a < k ? coef[a] : 0.0;
-        cs[a] = c;
-        if (PAIR) cs2[a] = a < k ? f2_neg(f2_split(c)) : F2(0.f);
-    }
+    for (int a = threadIdx.x; a < kMaxSub; a += kBlas) cs[a] = a < k ? coef[a] : 0.0;
     __syncthreads();
     double an = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)kBlas + threadIdx.x; i < N; i += (int64_t)gridDim.x * kBlas) {
-        double yn;
-        if constexpr (PAIR) {
-            F2 acc = f2_split(y[i]);
-            for (int a0 = 0; a0 < k; a0 += kLoad) {
-                double x[kLoad];
+        double s = 0.0;
+        for (int a0 = 0; a0 < k; a0 += kLoad) {
+            double x[kLoad];
 #pragma unroll
-                for (int u = 0; u < kLoad; ++u) x[u] = (a0 + u < k) ? X[(a0 + u) * ldx + i] : 0.0;
+            for (int u = 0; u < kLoad; ++u) x[u] = (a0 + u < k) ? X[(a0 + u) * ldx + i] : 0.0;
 #pragma unroll
-                for (int u = 0; u < kLoad; ++u)
-                    if (a0 + u < k) f2_mac(acc, cs2[a0 + u], f2_split(x[u]));
-            }
-            yn = f2_value(acc);
-        } else {
-            double s = 0.0;
-            for (int a0 = 0; a0 < k; a0 += kLoad) {
-                double x[kLoad];
-#pragma unroll
-                for (int u = 0; u < kLoad; ++u) x[u] = (a0 + u < k) ? X[(a0 + u) * ldx + i] : 0.0;
-#pragma unroll
-                for (int u = 0; u < kLoad; ++u) s += cs[min(a0 + u, kMaxSub - 1)] * x[u];
-            }
-            yn = y[i] - s;
+            for (int u = 0; u < kLoad; ++u) s += cs[min(a0 + u, kMaxSub - 1)] * x[u];
         }
+        const double yn = y[i] - s;
         y[i] = yn;
         if (NORM) an += yn * yn;
     }
@@ -425,7 +385,7 @@ struct Work {
     int64_t N;      // local vector length (this rank's rows in a sharded solve)
     int64_t off;    // global index of local element 0
     ShardCtx *sh;   // null: one process holds the whole vectors
-    bool pair = false;  // dot products, axpys and Ritz combinations in FP32 pairs (mixed solves)
+    bool pair = false;  // Ritz combinations (combine_kernel) summed in FP32 pairs
     int grid;
     double *partial = nullptr;  // [grid][kPart]
     double *dscal = nullptr;    // kMaxSub + 1 doubles: local dot products before the sum over ranks
@@ -481,49 +441,41 @@ struct Work {
         }
         local_dots(X, ldx, k, y, out1, st1, out2, st2, norm2);
     }
-    template <bool NORM, bool PAIR>
-    void launch_mdot(const double *Xa, int64_t ldx, int kb, const double *y)
-    {
-        if (kb <= 8) mdot_partial<NORM, 8, PAIR><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
-        else if (PAIR || kb <= 16) mdot_partial<NORM, 16, PAIR><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
-        else mdot_partial<NORM, kDotMax, false><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
-        SBD_LAUNCH("mdot_partial");
-    }
     void local_dots(const double *X, int64_t ldx, int k, const double *y, double *out1, int64_t st1,
                     double *out2, int64_t st2, double *norm2)
     {
-        // pair sums take twice the accumulator registers: at most 16 dot products per launch
-        const int step = pair ? 16 : kDotMax;
-        for (int a0 = 0; a0 < k || (a0 == 0 && norm2); a0 += step) {
-            const int kb = std::min(step, k - a0);
+        for (int a0 = 0; a0 < k || (a0 == 0 && norm2); a0 += kDotMax) {
+            const int kb = std::min(kDotMax, k - a0);
             const bool nrm = norm2 && a0 == 0;
             const double *Xa = X + a0 * ldx;
-            if (pair) {
-                if (nrm) launch_mdot<true, true>(Xa, ldx, kb, y);
-                else launch_mdot<false, true>(Xa, ldx, kb, y);
+            if (kb <= 8) {
+                if (nrm) mdot_partial<true, 8><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+                else mdot_partial<false, 8><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+            } else if (kb <= 16) {
+                if (nrm) mdot_partial<true, 16><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+                else mdot_partial<false, 16><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
             } else {
-                if (nrm) launch_mdot<true, false>(Xa, ldx, kb, y);
-                else launch_mdot<false, false>(Xa, ldx, kb, y);
+                if (nrm) mdot_partial<true, kDotMax><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+                else mdot_partial<false, kDotMax><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
             }
+            SBD_LAUNCH("mdot_partial");
             mdot_final<<<1, kDotMax + 1, 0, s>>>(partial, grid, kb, out1 + a0 * st1, st1,
                                                  out2 ? out2 + a0 * st2 : nullptr, st2, nrm ? norm2 : nullptr);
             SBD_LAUNCH("mdot_final");
-            if (k <= a0 + step) break;
+            if (k <= a0 + kDotMax) break;
         }
     }
     // y -= X coef; with norm2, also the new y . y
     void axpys(const double *X, int64_t ldx, int k, const double *coef, double *y, double *norm2 = nullptr)
     {
         if (norm2) {
-            if (pair) maxpy_kernel<true, true><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
-            else maxpy_kernel<true, false><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
+            maxpy_kernel<true><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
             SBD_LAUNCH("maxpy_kernel");
             mdot_final<<<1, kDotMax + 1, 0, s>>>(partial, grid, 0, nullptr, 0, nullptr, 0, norm2);
             SBD_LAUNCH("mdot_final");
             globalize(norm2, 1, 1);
         } else {
-            if (pair) maxpy_kernel<false, true><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
-            else maxpy_kernel<false, false><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
+            maxpy_kernel<false><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
             SBD_LAUNCH("maxpy_kernel");
         }
     }

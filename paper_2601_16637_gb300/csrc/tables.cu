@@ -390,10 +390,8 @@ __device__ bool joint_order(int64_t b, int64_t e, int64_t sb, int Lp, const int3
     while (q < L) {
         const int chunk = q / 32;
         const int m = min(32, Lp - chunk * 32) / 4;
-        const int nominal_end = q + m - (q - chunk * 32) % m;  // end of the phase q lies in
-        const int phase_end = min(L, nominal_end);
-        // padding slots (zero entries: target 0, key 0) in this phase already take residue 0 on both sides
-        unsigned int usedJ = nominal_end > L ? 1u : 0u, usedK = usedJ;
+        const int phase_end = min(L, q + m - (q - chunk * 32) % m);  // end of the phase q lies in
+        unsigned int usedJ = 0u, usedK = 0u;
         for (; q < phase_end; ++q) {
             int best = -1, best_score = -1, brj = 0, brk = 0;
             for (int x = 0; x < L; ++x) {
