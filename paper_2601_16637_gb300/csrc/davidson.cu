@@ -200,17 +200,18 @@ __global__ void __launch_bounds__(kBlas) combine_kernel(const double *__restrict
             }
 #pragma unroll
             for (int q = 0; q < kLoad / 2; ++q) {
-                const int a = min(a0 + q, kMaxSub - 1);
+                // coefficient rows a >= k were never written (stale shared memory): skip, do not
+                // multiply by the zero-filled x, h (a stale NaN or infinity would survive that)
+                if (a0 + q >= k) continue;
+                const int a = a0 + q;
                 if constexpr (PAIR) {
-                    if (a0 + q < k) {
-                        const F2 xs = f2_split(x[q]), hs = f2_split(h[q]);
+                    const F2 xs = f2_split(x[q]), hs = f2_split(h[q]);
 #pragma unroll
-                        for (int j = 0; j < M; ++j)
-                            if (j < m) {
-                                f2_mac(u[j], ys2[a * m + j], xs);
-                                f2_mac(hu[j], ys2[a * m + j], hs);
-                            }
-                    }
+                    for (int j = 0; j < M; ++j)
+                        if (j < m) {
+                            f2_mac(u[j], ys2[a * m + j], xs);
+                            f2_mac(hu[j], ys2[a * m + j], hs);
+                        }
                 } else {
 #pragma unroll
                     for (int j = 0; j < M; ++j)
