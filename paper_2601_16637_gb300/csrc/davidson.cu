@@ -5,8 +5,9 @@
 // Jacobi in one CTA), one fused pass for the Ritz vectors U = V Y, HU = W Y,
 // the residual norms and the preconditioned corrections
 // t = r / (sign(d) max(|d|, delta)), d = Hd - theta (Eq. 7); block classical
-// Gram-Schmidt with one re-orthogonalisation pass against the basis; and the
-// sigma product of the new basis vectors.  A thick restart keeps the lowest
+// Gram-Schmidt against the basis, with a second pass when the first removed
+// more than 1 - 1/sqrt(2) of the norm; and the sigma product of the new basis
+// vectors.  A thick restart keeps the lowest
 // Ritz vectors when the basis is full.
 //
 // All vectors, T, the Ritz quantities and every reduction are FP64 (two-stage

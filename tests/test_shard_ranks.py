@@ -117,3 +117,43 @@ def test_thread_ring_allreduce_is_identical_on_every_rank():
     expect = vals[0] + vals[1] + vals[2]
     for g in got:
         assert np.array_equal(g, got[0]) and np.array_equal(g, expect)
+
+
+def _distring_worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import ctypes
+
+    import torch.distributed as dist
+
+    from paper_2601_16637_gb300 import shard as S
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    comm = S.DistRing().comm()
+    vals = [1.0 + rank, -2.5 * rank, 1e-3 * (rank + 1), 7.0]
+    buf = (ctypes.c_double * 4)(*vals)
+    rc = comm.allreduce_sum(None, buf, 4)
+    q.put((rank, rc, comm.rank, comm.world, list(buf[:])))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_dist_ring_allreduce_callback_over_gloo_ranks():
+    # the host side of the torch.distributed communicator handed to sbd_davidson_sharded: the
+    # allreduce callback sums host doubles over the group (gloo: on CPU tensors)
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_distring_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(world))
+    expect = [sum(1.0 + r for r in range(world)), sum(-2.5 * r for r in range(world)),
+              sum(1e-3 * (r + 1) for r in range(world)), 7.0 * world]
+    for rank, rc, crank, cworld, got in res:
+        assert rc == 0 and crank == rank and cworld == world
+        assert np.allclose(got, expect, rtol=1e-15, atol=0)
+        assert got == res[0][4]  # every rank holds the same bits
