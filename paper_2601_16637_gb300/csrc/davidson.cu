@@ -797,7 +797,7 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
                 const bool stalled = since_ref > 8 && rmax > 0.5 * hist[hist.size() - 9] && rmax < 1e-4 * thmax;
                 if (rmax <= std::max(tol, floor_now) || stalled || iter >= max_iter) {
                     // defect correction: keep the lowest Ritz vectors, replace the target
-                    // columns' W by the FP64 sigma, judge convergence on FP64 residuals
+                    // columns' W by the FP64 sigma, decide convergence on FP64 residuals
                     const int nk = std::min(std::max(nkeep, nroots), k);
                     compress(k, nk);
                     sigma_cols(0, nroots, true);
