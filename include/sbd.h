@@ -311,8 +311,10 @@ int sbd_block_plan_destroy(sbd_block_plan plan);
  *   allreduce_sum(ctx, buf, n): replace the n host doubles in buf by their sum over the ranks;
  *   ring_exchange(ctx, send, send_bytes, recv, recv_bytes, stream): send the device buffer `send` to
  *     rank (rank+1) mod world and receive into the device buffer `recv` from rank (rank-1) mod world;
- *     work on `stream` before the call is complete when it is made, and `recv` must hold the data
- *     when the callback returns.
+ *     `send` holds its data when the call is made, and `recv` must hold the data when the callback
+ *     returns.  The products of the block in `send` may still be running on `stream` during the call
+ *     (the transfer overlaps them, double buffering): the callback must not write `send`; `recv` is
+ *     not in use by the library until the callback returns.
  */
 typedef struct {
     int rank, world;

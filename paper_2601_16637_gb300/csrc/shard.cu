@@ -258,20 +258,25 @@ void ring_sigma(ShardCtx &sh, Ctx &c, const void *x_rows, double *y_rows, sbd_pr
     const size_t elem = prec == SBD_MIXED ? sizeof(float) : sizeof(double);
     const int W = sh.world, r = sh.rank;
     SBD_CUDA(cudaMemsetAsync(y_rows, 0, sizeof(double) * (size_t)sh.rows() * (size_t)c.nB, s));
+    // the rank's own block is complete before the first transfer reads it
+    SBD_CUDA(cudaStreamSynchronize(s));
     const void *cur = x_rows;
     for (int step = 0; step < W; ++step) {
         const int b = ((r - step) % W + W) % W;
         sigma_block_apply(*sh.plans[b], cur, y_rows, prec, s, b == r ? x64_rows : nullptr);
+        void *nxt = nullptr;
         if (step + 1 < W) {
+            // double buffering (Sec. III-E): the transfer runs while the products above are in flight.
+            // Both only read cur; nxt was last read by the previous step's products, which have completed.
             const int nb = ((r - step - 1) % W + W) % W;
-            void *nxt = sh.ring[step % 2];
+            nxt = sh.ring[step % 2];
             const size_t sb = (size_t)(sh.bounds[b + 1] - sh.bounds[b]) * (size_t)c.nB * elem;
             const size_t rb = (size_t)(sh.bounds[nb + 1] - sh.bounds[nb]) * (size_t)c.nB * elem;
-            SBD_CUDA(cudaStreamSynchronize(s));  // the callback may read cur at once
             if (sh.comm.ring_exchange(sh.comm.ctx, cur, sb, nxt, rb, (void *)s) != 0)
                 fail(SBD_ERR_CUDA, "ring_exchange callback failed");
-            cur = nxt;
         }
+        SBD_CUDA(cudaStreamSynchronize(s));  // this block's products are done before its buffer is reused
+        if (nxt) cur = nxt;
     }
 }
 
