@@ -410,6 +410,17 @@ def test_error_duplicate_bad_string_and_nonfinite(torch, B):
     assert e.value.code == -8
 
 
+def test_error_more_strings_than_the_packed_lists_hold(torch, B):
+    # the sigma lists pack a string index in 18 bits: 2^18 strings per spin is one too many
+    norb, n = 22, 8
+    A = W.all_strings(norb, n)[: 1 << 18]
+    Bs = W.all_strings(norb, 1)[:3]
+    h, eri = W.one_electron(norb, 3), W.two_electron(norb, 3)
+    with pytest.raises(B.SbdError) as e:
+        B.SBD(norb, n, 1, h, eri, A, Bs)
+    assert e.value.code == -10  # SBD_ERR_UNSUPPORTED
+
+
 def test_error_budget_and_failing_allocator(torch, B):
     wl = W.make("t", 10, 3, 3, 30, 30, 0.3, seed=2)
     with pytest.raises(B.SbdError) as e:
