@@ -1,0 +1,44 @@
+"""Host-side helpers of bench.py (no GPU): the nvidia-smi clock-sample parser that decides whether a
+run saw throttling, and the lookup of committed DRAM-traffic records by kernel source digest."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_clock_samples_median_max_and_reasons():
+    lines = [
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "0, 1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n",
+        "0, 2070, 2070, 1200.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "garbage line\n",
+        "0, N/A, 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active\n",
+    ]
+    out = bench.parse_clock_samples(lines)
+    assert out["samples"] == 3 and out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+    hot = bench.parse_clock_samples(["0, 1500, 2070, 1400, 0x48, Active, Active, Not Active, Not Active"])
+    assert hot["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"] and hot["sm_mhz"] == 1500.0
+    empty = bench.parse_clock_samples([])
+    assert empty["sm_mhz"] is None and empty["samples"] == 0
+
+
+def test_traffic_record_matches_only_the_current_kernel_source():
+    digest = bench.kernel_source_digest()
+    assert len(digest) == 16 and all(c in "0123456789abcdef" for c in digest)
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    recorded = {}
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and not line.startswith("#"):
+            recorded[(parts[0], parts[1])] = float(parts[2])
+    got = bench.traffic_record("ab_pass_mixed")
+    if ("ab_pass_mixed", digest) in recorded:
+        assert got == recorded[("ab_pass_mixed", digest)]
+    else:
+        assert got is None  # a record taken on other kernel source is not reported
+    assert bench.traffic_record("no_such_kernel") is None
