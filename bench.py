@@ -646,7 +646,11 @@ def main():
                 "parallelism": "replicas" if world > 1 else "single GPU",
                 "solves_per_s": solves_per_s, "sigma_applications_per_step": n_sigma / args.steps,
                 "sigma_only_dets_per_s": sigma_rate, "energy_Ha": float(energies[0]),
-                "residual": float(resid[0]), "kernels": kern, "mixed_vs_fp64": mixed_vs_fp64,
+                "residual": float(resid[0]),
+                # Kato-Temple-form estimate of the energy error: residual^2 / (next Ritz value - energy)
+                "energy_error_estimate_Ha": (float(resid[0]) ** 2 / reports[-1]["gap_estimate"]
+                                             if reports[-1].get("gap_estimate", 0.0) > 0.0 else None),
+                "kernels": kern, "mixed_vs_fp64": mixed_vs_fp64,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk, "last_report": reports[-1]}
         print(json.dumps(line), flush=True)

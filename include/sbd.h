@@ -109,6 +109,10 @@ typedef struct {
     double max_residual;  /* largest final residual norm (FP64-evaluated) */
     double seconds_total; /* wall time inside sbd_davidson */
     double seconds_sigma; /* of which sigma launches (host-timed with events) */
+    double gap_estimate;  /* first Ritz value above the roots minus the highest root's Ritz value at
+                             the last Rayleigh-Ritz step (0 if the basis held no further vector);
+                             residual_j^2 / (gap_estimate + E_last - E_j) estimates the error of
+                             energy j (Kato-Temple form, with a Ritz value for the next eigenvalue) */
 } sbd_report;
 
 /* Fills *opt with the defaults listed above. */

@@ -48,7 +48,8 @@ class sbd_report(C.Structure):
     _fields_ = [("iterations", C.c_int), ("sigma_fp64", C.c_int), ("sigma_mixed", C.c_int),
                 ("restarts", C.c_int), ("refinements", C.c_int), ("reorthogonalisations", C.c_int),
                 ("status", C.c_int),
-                ("max_residual", C.c_double), ("seconds_total", C.c_double), ("seconds_sigma", C.c_double)]
+                ("max_residual", C.c_double), ("seconds_total", C.c_double), ("seconds_sigma", C.c_double),
+                ("gap_estimate", C.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -769,6 +769,7 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
         rebuild_T(k);
 
         std::vector<double> th(kMaxSub), rn(nroots), hist, th_prev;
+        int k_ritz = 0;  // th[0..k_ritz) are the Ritz values of the last Rayleigh-Ritz step
         bool converged = false;
         double switch_floor = -1.0;  // mixed: residual level that triggers an FP64 check
         int since_ref = 0;
@@ -781,6 +782,7 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
             w.ritz(V, W, ld, k, Y, kMaxSub, nroots, U, HU, theta, hd, delta, TC, rn.data());
             SBD_CUDA(cudaMemcpyAsync(th.data(), theta, sizeof(double) * k, cudaMemcpyDeviceToHost, w.s));
             SBD_CUDA(cudaStreamSynchronize(w.s));
+            k_ritz = k;
             harvest_timing(c);
             double rmax = *std::max_element(rn.begin(), rn.end());
             if (c.opt.verbose)
@@ -907,6 +909,8 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
             rmax = std::max(rmax, rn[j]);
         }
         r.max_residual = rmax;
+        // the first Ritz value above the roots bounds the next eigenvalue from above (interlacing)
+        r.gap_estimate = k_ritz > nroots ? th[nroots] - th[nroots - 1] : 0.0;
         if (vecs)
             SBD_CUDA(cudaMemcpyAsync(vecs, U, (size_t)nroots * N * sizeof(double), cudaMemcpyDefault, w.s));
         SBD_CUDA(cudaStreamSynchronize(w.s));

@@ -304,6 +304,8 @@ def test_davidson_cfg1_against_dense(torch, B, oracle_mod):
         # eigenvector: residual against the oracle sigma
         r = o.sigma(u[None, :])[0] - res.energies[0] * u
         assert np.linalg.norm(r) <= 10 * wl.tol
+        # the first Ritz value above the root is an upper bound of the second eigenvalue (interlacing)
+        assert res.report["gap_estimate"] >= (ref[1] - ref[0]) - 1e-8
 
 
 @pytest.fixture(scope="module")
