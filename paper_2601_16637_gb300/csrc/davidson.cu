@@ -7,8 +7,8 @@
 // t = r / (sign(d) max(|d|, delta)), d = Hd - theta (Eq. 7); block classical
 // Gram-Schmidt against the basis, with a second pass when the first removed
 // more than 1 - 1/sqrt(2) of the norm; and the sigma product of the new basis
-// vectors.  A thick restart keeps the lowest
-// Ritz vectors when the basis is full.
+// vectors.  A thick restart keeps the lowest Ritz vectors when the basis is
+// full.
 //
 // All vectors, T, the Ritz quantities and every reduction are FP64 (two-stage
 // reductions in a fixed order, so results are reproducible).  In mixed mode

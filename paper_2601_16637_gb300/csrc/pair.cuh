@@ -2,7 +2,7 @@
 // FP64-accurate arithmetic on the FP32 pipe: a value is the unevaluated sum hi + lo of two floats.
 // Products are exact hi*hi (a fused multiply-add recovers its rounding error, Dekker's product) plus
 // the two cross terms; sums use Knuth's two-sum.  On GB300 the FP32 pipe is ~64x the FP64 pipe, so
-// the FP64-accurate sigma and the Davidson vector kernels of mixed solves run on these pairs.
+// the FP64-accurate sigma and the Davidson solver's Ritz combinations run on these pairs.
 
 #include "common.cuh"
 
