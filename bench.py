@@ -45,6 +45,9 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0
 NUM_SMS = 152
 FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25
+# sigma products of the FP64 3-root solve of the 4.0e6-determinant instance (cfg2) on the GPU, the
+# count the oracle Davidson time of that instance is extrapolated with
+CFG2_FP64_SIGMA_COUNT = 446
 
 
 def load_peaks():
@@ -60,15 +63,40 @@ def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def nvsmi_gpu_id(device: int, props=None, visible: str | None = None) -> str:
+    """The nvidia-smi `-i` argument for CUDA device `device` of this process.  nvidia-smi numbers GPUs
+    by physical index and ignores CUDA_VISIBLE_DEVICES, so the device is named by its UUID
+    ("GPU-<uuid>"); without one, a CUDA_VISIBLE_DEVICES entry is mapped back to what it names."""
+    if props is None:
+        try:
+            import torch
+
+            props = torch.cuda.get_device_properties(device)
+        except Exception:
+            props = None
+    uuid = getattr(props, "uuid", None) if props is not None else None
+    if uuid:
+        u = str(uuid)
+        return u if u.startswith(("GPU-", "MIG-")) else "GPU-" + u
+    if visible is None:
+        visible = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if visible:
+        ent = [x.strip() for x in visible.split(",") if x.strip()]
+        if 0 <= device < len(ent):
+            return ent[device]
+    return str(device)
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region on the GPU that CUDA
+    device `device` of this process is."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+    def __init__(self, device: int):
+        self.gpu = nvsmi_gpu_id(device)
         self.proc = None
         self.path = None
 
@@ -76,7 +104,7 @@ class ClockSampler:
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu, f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
@@ -115,6 +143,17 @@ def parse_clock_samples(lines) -> dict:
                 reasons.add(n)
     return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
             "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def energy_error_estimates(energies, residuals, report) -> list:
+    """Per root j the Kato-Temple-form error estimate residual_j^2 / (gap + E_last - E_j), gap being
+    the report's gap_estimate (first Ritz value above the roots minus the highest root); None for
+    every root when no gap was recorded."""
+    gap = float(report.get("gap_estimate", 0.0) or 0.0)
+    if not gap > 0.0:
+        return [None] * len(energies)
+    last = float(energies[-1])
+    return [float(r) ** 2 / (gap + last - float(e)) for e, r in zip(energies, residuals)]
 
 
 def max_over_ranks(value: float, world: int) -> float:
@@ -177,6 +216,53 @@ def oracle_rows_rate(wl, budget_s: float, seed: int = 0):
         batch = int(min(2 * batch, max(64, batch * left / max(step, 1e-9))))
     o.close()
     return nrows / dt, nrows, dt, threads
+
+
+def oracle_extras(cfg3_rate: float, cfg3_ndets: int, cfg2_sigma_count: int | None = None,
+                  full_cfg2: bool = False, cfg2_seconds: float = 5.0) -> dict:
+    """Oracle timings on the host cores beside the bounded sample: one full sigma and the full
+    Davidson on the full-space norb=8 instance (cfg1); on the 4.0e6-determinant instance (cfg2) one
+    full sigma when full_cfg2 (minutes of CPU time), else sigma rows sampled for cfg2_seconds and
+    extrapolated to one sigma.  The oracle Davidson on cfg2 (hundreds of sigma products, about a day
+    of CPU time) and one sigma on the 1.0e8-determinant instance are not run: they are extrapolated
+    from the sigma time and the sampled row rate, and labelled as such."""
+    from oracle import oracle as O
+    from paper_2601_16637_gb300 import workloads as W
+
+    O.build()
+    out = {"threads": O.num_threads()}
+    for name in ("cfg1", "cfg2"):
+        wl = W.config(name)
+        if name == "cfg2" and not full_cfg2:
+            rate, nrows, dt, _ = oracle_rows_rate(wl, cfg2_seconds)
+            ts = wl.ndets / rate
+            out[name] = {"ndets": int(wl.ndets), "sigma_s_extrapolated": ts, "sigma_dets_per_s": rate,
+                         "note": f"extrapolated, not run: {nrows} sampled sigma rows in {dt:.1f} s"}
+            if cfg2_sigma_count:
+                out[name]["davidson_s_extrapolated"] = ts * cfg2_sigma_count
+                out[name]["davidson_note"] = (f"extrapolated, not run: sigma time x {cfg2_sigma_count} sigma "
+                                              f"products (the GPU FP64 solve of this instance)")
+            continue
+        o = O.Oracle.from_workload(wl)
+        x = W.random_vector(o.N, 100)
+        t0 = time.perf_counter()
+        o.sigma(x)
+        ts = time.perf_counter() - t0
+        out[name] = {"ndets": int(wl.ndets), "sigma_s": ts, "sigma_dets_per_s": wl.ndets / ts}
+        if name == "cfg1":
+            t0 = time.perf_counter()
+            e, _, r, it = o.davidson(nroots=wl.nroots, tol=wl.tol)
+            out[name]["davidson_s"] = time.perf_counter() - t0
+            out[name]["davidson_iterations"] = int(it)
+            out[name]["davidson_energy_Ha"] = float(e[0])
+        elif cfg2_sigma_count:
+            out[name]["davidson_s_extrapolated"] = ts * cfg2_sigma_count
+            out[name]["davidson_note"] = (f"extrapolated, not run: measured sigma time x {cfg2_sigma_count} sigma "
+                                          f"products (the GPU FP64 solve of this instance)")
+        o.close()
+    out["cfg3"] = {"ndets": int(cfg3_ndets), "sigma_s_extrapolated": cfg3_ndets / cfg3_rate,
+                   "note": "extrapolated, not run: determinants / the sampled sigma-row rate"}
+    return out
 
 
 def run_reference(args):
@@ -262,28 +348,23 @@ def engine_line(args, metric_value, elapsed, n_jobs, stats, extra, clk, config):
             "graph_launches": int(stats["graph_launches"]), "engine": stats, "clocks": clk, **extra}
 
 
-def run_batch(args):
-    """64 independent instances in one engine (persistent launches, CUDA graphs), against the
-    serial FP64 per-instance path on the same instances and stopping rule."""
+def batch_measure(B, insts, subspace: int, warmup: int, steps: int) -> dict:
+    """One engine run over `insts` (persistent launches, CUDA graphs), `steps` times after `warmup`
+    untimed runs on the two smallest instances, against the serial FP64 per-instance path on the
+    same instances and stopping rule.  solves/s count converged jobs only (status 0)."""
     import torch
 
-    from paper_2601_16637_gb300 import binding as B
-    from paper_2601_16637_gb300 import workloads as W
-
-    B.load(build_if_missing=True)
-    insts = W.batch_instances(args.batch_n)
-    opts = dict(max_slots=len(insts), max_subspace=args.engine_subspace, max_norb=26, max_strings=5000, max_iter=400)
+    opts = dict(max_slots=len(insts), max_subspace=subspace, max_norb=max(w.norb for w in insts),
+                max_strings=max(max(w.A.size, w.B.size) for w in insts), max_iter=400)
     small = sorted(insts, key=lambda w: w.ndets)[:2]
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         with B.Engine(**opts) as e:
             for w in small:
                 e.submit(w, tol=w.tol, tol_energy=w.extra["tol_energy"])
             e.run()
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
-    clocks.start()
     elapsed, dets_sigma, results, stats = 0.0, 0.0, [], None
-    for _ in range(args.steps):
+    for _ in range(steps):
         t0 = time.perf_counter()
         with B.Engine(**opts) as e:
             ids = [e.submit(w, tol=w.tol, tol_energy=w.extra["tol_energy"]) for w in insts]
@@ -293,7 +374,6 @@ def run_batch(args):
             results = [e.result(j) for j in ids]
             stats = e.stats()
         dets_sigma += sum(r["ndets"] * (r["sigma_mixed"] + r["sigma_fp64"]) for r in results)
-    clk = clocks.stop()
     stream = torch.cuda.current_stream()
     serial_t, dE, serial_status, serial_it = 0.0, 0.0, [], []
     for w, r in zip(insts, results):
@@ -301,29 +381,47 @@ def run_batch(args):
         serial_t += t
         serial_status.append(st)
         serial_it.append(rep["iterations"])
-        dE = max(dE, abs(e64 - r["energy"]))
-    per_run = elapsed / args.steps
-    extra = {"batch": {"instances": len(insts), "total_dets": int(sum(w.ndets for w in insts)),
-                       "status_counts": {str(k): sum(1 for r in results if r["status"] == k)
-                                         for k in sorted({r["status"] for r in results})},
-                       "iterations_min_median_max": [int(np.min([r["iterations"] for r in results])),
-                                                     float(np.median([r["iterations"] for r in results])),
-                                                     int(np.max([r["iterations"] for r in results]))],
-                       "max_subspace": args.engine_subspace,
-                       "seconds_per_batch": per_run},
-             "vs_serial_fp64": {"seconds": serial_t, "solves_per_s": len(insts) / serial_t,
-                                "iterations_min_median_max": [int(np.min(serial_it)), float(np.median(serial_it)),
-                                                              int(np.max(serial_it))],
-                                "speedup": serial_t / per_run, "max_abs_dE_Ha": dE,
-                                "statuses": {str(k): serial_status.count(k) for k in sorted(set(serial_status))}}}
+        if st == 0 and r["status"] == 0:
+            dE = max(dE, abs(e64 - r["energy"]))
+    per_run = elapsed / steps
+    conv = sum(1 for r in results if r["status"] == 0)
+    conv64 = sum(1 for x in serial_status if x == 0)
+    its = [r["iterations"] for r in results]
+    return {"elapsed": elapsed, "dets_sigma": dets_sigma, "stats": stats, "per_run": per_run,
+            "summary": {"instances": len(insts), "total_dets": int(sum(w.ndets for w in insts)),
+                        "converged": conv, "solves_per_s": conv / per_run, "seconds_per_batch": per_run,
+                        "status_counts": {str(k): sum(1 for r in results if r["status"] == k)
+                                          for k in sorted({r["status"] for r in results})},
+                        "iterations_min_median_max": [int(np.min(its)), float(np.median(its)), int(np.max(its))],
+                        "max_subspace": subspace, "rows_per_item": stats["rows_per_item"]},
+            "vs_serial_fp64": {"seconds": serial_t, "converged": conv64, "solves_per_s": conv64 / serial_t,
+                               "iterations_min_median_max": [int(np.min(serial_it)), float(np.median(serial_it)),
+                                                             int(np.max(serial_it))],
+                               "speedup": serial_t / per_run, "max_abs_dE_Ha": dE,
+                               "statuses": {str(k): serial_status.count(k) for k in sorted(set(serial_status))}}}
+
+
+def run_batch(args):
+    """64 independent instances in one engine (persistent launches, CUDA graphs), against the
+    serial FP64 per-instance path on the same instances and stopping rule."""
+    from paper_2601_16637_gb300 import binding as B
+    from paper_2601_16637_gb300 import workloads as W
+
+    B.load(build_if_missing=True)
+    insts = W.batch_instances(args.batch_n)
+    clocks = ClockSampler(0)
+    clocks.start()
+    m = batch_measure(B, insts, args.engine_subspace, args.warmup, args.steps)
+    clk = clocks.stop()
+    extra = {"batch": m["summary"], "vs_serial_fp64": m["vs_serial_fp64"]}
     config = {"workload": f"batch{len(insts)}: {len(insts)} instances, norb in {{16,20,24,26}}, "
                           f"nalpha=nbeta=round(norb/3), |A|,|B| uniform in [500,5000], own integrals each; "
                           f"1 root, mixed sigma, residual <= {insts[0].tol:g} and Ritz-value change <= 1e-6 Ha",
               "step": "one engine run over all instances (admission, tables, Davidson, FP64 check)",
-              "max_subspace": args.engine_subspace, "rows_per_item": stats["rows_per_item"],
+              "max_subspace": args.engine_subspace, "rows_per_item": m["stats"]["rows_per_item"],
               "l2": "inputs larger than L2 (vectors of all instances ~4 GB)"}
-    print(json.dumps(engine_line(args, dets_sigma / elapsed, elapsed, len(insts) * args.steps, stats, extra, clk,
-                                 config)), flush=True)
+    print(json.dumps(engine_line(args, m["dets_sigma"] / m["elapsed"], m["elapsed"],
+                                 m["summary"]["converged"] * args.steps, m["stats"], extra, clk, config)), flush=True)
     return 0
 
 
@@ -350,34 +448,21 @@ def serve_once(B, opts, jobs):
         return results, base, e.stats()
 
 
-def run_serve(args):
-    """A finite Poisson stream of jobs served by one engine (continuous batching under a memory
-    budget), against a FIFO queue served one job at a time by the serial FP64 path, for each of the
-    arrival rates given (the same jobs; only the arrival times scale with the rate)."""
+def serve_measure(B, built, traces, rates, subspace: int, budget_bytes: int, max_strings: int, warmup: int) -> dict:
+    """Serves the jobs `built` (arrival times traces[rate]) with one engine per rate (continuous
+    batching under a memory budget), and a FIFO queue served one job at a time by the serial FP64
+    path on the same arrivals (measured service time per job).  Latencies count from arrival."""
     import torch
 
-    from paper_2601_16637_gb300 import binding as B
-    from paper_2601_16637_gb300 import workloads as W
-
-    B.load(build_if_missing=True)
-    rates = [float(r) for r in str(args.rates).split(",")] if args.rates else [args.rate]
-    traces = {r: W.serving_trace(n=args.requests, rate=r, max_strings=args.max_strings) for r in rates}
-    t_build = time.perf_counter()
-    specs = traces[rates[0]]
-    built = [W.make_job(spec, te) for _, spec, te in specs]
-    t_build = time.perf_counter() - t_build
-    max_norb = max(w.norb for w in built)
-    opts = dict(max_slots=64, max_subspace=args.engine_subspace, max_norb=max_norb, max_strings=args.max_strings,
-                max_iter=400, hbm_budget_bytes=int(args.budget_gb * 1e9))
+    opts = dict(max_slots=64, max_subspace=subspace, max_norb=max(w.norb for w in built), max_strings=max_strings,
+                max_iter=400, hbm_budget_bytes=int(budget_bytes))
     small = sorted(built, key=lambda w: w.ndets)[:2]
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         with B.Engine(**opts) as e:
             for w in small:
                 e.submit(w, tol=w.tol, tol_energy=w.extra["tol_energy"])
             e.run()
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
-    clocks.start()
     runs = []
     for r in rates:
         jobs = [(t, w) for (t, _, _), w in zip(traces[r], built)]
@@ -385,49 +470,92 @@ def run_serve(args):
         arrivals = np.array([t for t, _ in jobs])
         done = np.array([x["t_done"] - base for x in results])
         runs.append((r, arrivals, done, results, stats))
-    clk = clocks.stop()
-    # serial FP64 per-instance path: measured service time per job, FIFO queue on the same arrivals
     stream = torch.cuda.current_stream()
     service, dE, st64 = [], 0.0, []
     for w, res in zip(built, runs[0][3]):
         ts, e64, st, _ = serial_fp64(B, w, stream)
         service.append(ts)
         st64.append(st)
-        dE = max(dE, abs(e64 - res["energy"]))
+        if st == 0 and res["status"] == 0:
+            dE = max(dE, abs(e64 - res["energy"]))
     sweep = []
     n = len(built)
     for r, arrivals, done, results, stats in runs:
         lat = done - arrivals
         span = float(done.max() - arrivals.min())
+        conv = sum(1 for x in results if x["status"] == 0)
         fin, tcur = [], 0.0
         for a, sv in zip(arrivals, service):
             tcur = max(tcur, a) + sv
             fin.append(tcur)
         lat64 = np.array(fin) - arrivals
         span64 = float(fin[-1] - arrivals.min())
+        conv64 = sum(1 for x in st64 if x == 0)
         sweep.append({"rate_per_s": r, "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                      "makespan_s": span, "solves_per_s": n / span, "bytes_peak": stats["bytes_peak"],
+                      "makespan_s": span, "converged": conv, "solves_per_s": conv / span,
+                      "bytes_peak": stats["bytes_peak"], "requeued": stats.get("requeued", 0),
                       "status_counts": {str(k): sum(1 for x in results if x["status"] == k)
                                         for k in sorted({x["status"] for x in results})},
                       "serial_fp64": {"p50_s": float(np.percentile(lat64, 50)), "p99_s": float(np.percentile(lat64, 99)),
-                                      "makespan_s": span64, "solves_per_s": n / span64}})
+                                      "makespan_s": span64, "converged": conv64, "solves_per_s": conv64 / span64}})
     r0, arrivals, done, results, stats = runs[0]
     span = float(done.max() - arrivals.min())
     dets_sigma = sum(x["ndets"] * (x["sigma_mixed"] + x["sigma_fp64"]) for x in results)
-    extra = {"serving": {"requests": n, "rate_per_s": r0, "p50_s": sweep[0]["p50_s"], "p99_s": sweep[0]["p99_s"],
-                         "makespan_s": span, "status_counts": sweep[0]["status_counts"],
-                         "bytes_peak": stats["bytes_peak"], "budget_bytes": opts["hbm_budget_bytes"],
-                         "job_build_s": t_build, "sweep": sweep},
-             "vs_serial_fp64": {**sweep[0]["serial_fp64"], "service_s_total": float(sum(service)),
-                                "max_abs_dE_Ha": dE, "statuses": {str(k): st64.count(k) for k in sorted(set(st64))}}}
-    config = {"workload": f"serve: {n} Poisson arrivals at {r0:g}/s, norb in {{24,32,40,48,58}}, "
-                          f"nalpha=nbeta=round(norb/3), |A|=|B| log-uniform in [300,{args.max_strings}], own "
-                          f"integrals each; 1 root, mixed sigma, residual <= {built[0].tol:g} and Ritz-value change "
-                          f"<= 1e-6 Ha; admission budget {args.budget_gb:g} GB",
+    return {"span": span, "dets_sigma": dets_sigma, "stats": stats, "n": n,
+            "serving": {"requests": n, "rate_per_s": r0, "p50_s": sweep[0]["p50_s"], "p99_s": sweep[0]["p99_s"],
+                        "makespan_s": span, "converged": sweep[0]["converged"],
+                        "solves_per_s": sweep[0]["solves_per_s"], "status_counts": sweep[0]["status_counts"],
+                        "bytes_peak": stats["bytes_peak"], "budget_bytes": opts["hbm_budget_bytes"],
+                        "largest_job_dets": int(max(w.ndets for w in built)),
+                        "largest_norb": int(max(w.norb for w in built)), "sweep": sweep},
+            "vs_serial_fp64": {**sweep[0]["serial_fp64"], "service_s_total": float(sum(service)),
+                               "max_abs_dE_Ha": dE, "statuses": {str(k): st64.count(k) for k in sorted(set(st64))}}}
+
+
+def serve_jobs(requests: int, rates, max_strings: int, big: int = 0, big_strings: int = 15000, big_norb: int = 58):
+    """The serving trace (seeded Poisson arrivals, workloads.serving_trace) for each rate, its jobs
+    built once; `big` extra jobs at the top of the configuration's range (norb big_norb,
+    |A| = |B| = big_strings) replace the last ones of the trace, keeping their arrival times."""
+    from paper_2601_16637_gb300 import workloads as W
+
+    traces = {r: W.serving_trace(n=requests, rate=r, max_strings=max_strings) for r in rates}
+    specs = [dict(spec) for _, spec, _ in traces[rates[0]]]
+    for i in range(big):
+        sp = specs[requests - 1 - i]
+        nel = int(round(big_norb / 3))
+        sp.update(name=f"serve-big-{i}", norb=big_norb, nalpha=nel, nbeta=nel, nA=big_strings, nB=big_strings)
+    t0 = time.perf_counter()
+    built = [W.make_job(sp, te) for sp, (_, _, te) in zip(specs, traces[rates[0]])]
+    return traces, built, time.perf_counter() - t0
+
+
+def run_serve(args):
+    """A finite Poisson stream of jobs served by one engine (continuous batching under a memory
+    budget), against a FIFO queue served one job at a time by the serial FP64 path, for each of the
+    arrival rates given (the same jobs; only the arrival times scale with the rate)."""
+    from paper_2601_16637_gb300 import binding as B
+
+    B.load(build_if_missing=True)
+    rates = [float(r) for r in str(args.rates).split(",")] if args.rates else [args.rate]
+    traces, built, t_build = serve_jobs(args.requests, rates, args.max_strings, big=args.serve_big)
+    clocks = ClockSampler(0)
+    clocks.start()
+    m = serve_measure(B, built, traces, rates, args.engine_subspace, int(args.budget_gb * 1e9),
+                      max(args.max_strings, 15000 if args.serve_big else 0), args.warmup)
+    clk = clocks.stop()
+    m["serving"]["job_build_s"] = t_build
+    extra = {"serving": m["serving"], "vs_serial_fp64": m["vs_serial_fp64"]}
+    n = m["n"]
+    config = {"workload": f"serve: {n} Poisson arrivals at {rates[0]:g}/s, norb in {{24,32,40,48,58}}, "
+                          f"nalpha=nbeta=round(norb/3), |A|=|B| log-uniform in [300,{args.max_strings}]"
+                          + (f" with the last {args.serve_big} jobs at norb 58, |A|=|B|=15,000" if args.serve_big else "")
+                          + f", own integrals each; 1 root, mixed sigma, residual <= {built[0].tol:g} and Ritz-value "
+                          f"change <= 1e-6 Ha; admission budget {args.budget_gb:g} GB",
               "step": "the whole trace (arrival of the first job to completion of the last)",
               "l2": "inputs larger than L2"}
     args.steps = 1
-    print(json.dumps(engine_line(args, dets_sigma / span, span, n, stats, extra, clk, config)), flush=True)
+    print(json.dumps(engine_line(args, m["dets_sigma"] / m["span"], m["span"], m["serving"]["converged"], m["stats"],
+                                 extra, clk, config)), flush=True)
     return 0
 
 
@@ -442,6 +570,9 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="solves timed end to end (at most --steps)")
+    ap.add_argument("--no-oracle-extras", action="store_true", help="skip the oracle sigma/Davidson timings")
+    ap.add_argument("--oracle-full", action="store_true", help="time one full oracle sigma of cfg2 (minutes)")
     ap.add_argument("--batch-n", type=int, default=64, help="instances of the batch64 workload")
     ap.add_argument("--requests", type=int, default=40, help="jobs of the serve workload")
     ap.add_argument("--rate", type=float, default=20.0, help="arrivals per second of the serve workload")
@@ -449,6 +580,12 @@ def main():
     ap.add_argument("--max-strings", type=int, default=5000, help="largest |A| = |B| of the serve workload")
     ap.add_argument("--budget-gb", type=float, default=160.0, help="engine admission budget of the serve workload")
     ap.add_argument("--engine-subspace", type=int, default=20, help="Davidson basis per job in the engine")
+    ap.add_argument("--serve-big", type=int, default=0,
+                    help="serve workload: the last N jobs at norb 58, |A|=|B|=15,000 (the top of its range)")
+    ap.add_argument("--legs", default="batch,serve",
+                    help="default line: engine legs to add (comma-separated: batch, serve; empty for none)")
+    ap.add_argument("--leg-batch-n", type=int, default=16, help="instances of the batched leg")
+    ap.add_argument("--leg-requests", type=int, default=24, help="jobs of the served leg")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -486,15 +623,17 @@ def main():
     vec_d = torch.empty((wl.nroots, wl.ndets), dtype=torch.float64, device="cuda")
     alloc = B._TorchAllocator()
 
-    def options(timing=True):
+    def options(timing=True, refine=None):
         o = B.sbd_default_options()
         o.max_subspace = wl.max_subspace
         o.timing = int(timing)
         o.alloc, o.free = alloc.alloc, alloc.free
+        if refine is not None:
+            o.refine_precision = B.PRECISION[refine]
         return o
 
-    def step(h, eri, A, Bs, vec, precision=prec):
-        handle = B.sbd_create(wl.norb, wl.nalpha, wl.nbeta, h, eri, A, Bs, options(), stream)
+    def step(h, eri, A, Bs, vec, precision=prec, refine=None):
+        handle = B.sbd_create(wl.norb, wl.nalpha, wl.nbeta, h, eri, A, Bs, options(refine=refine), stream)
         e = np.empty(wl.nroots)
         r = np.empty(wl.nroots)
         rc, rep = B.sbd_davidson(handle, wl.nroots, wl.tol, precision, e, vec, r)
@@ -604,6 +743,17 @@ def main():
                          "abs_diff_Ha": float(abs(energies[0] - e64[0])),
                          "solve_s_mixed": reports[-1]["seconds_total"], "solve_s_fp64": rep64["seconds_total"],
                          "speedup": rep64["seconds_total"] / reports[-1]["seconds_total"]}
+        # the literal reading of the precision statement: the defect corrections (and the Ritz
+        # combinations of the refined solve) in IEEE FP64 instead of FP32 pairs
+        el, rl, repl, _, _ = step(h_d, eri_d, A_d, B_d, vec_d, refine="fp64")
+        mixed_vs_fp64["refine_fp64"] = {"E": float(el[0]), "abs_diff_Ha": float(abs(el[0] - e64[0])),
+                                        "residual": float(rl[0]), "solve_s": repl["seconds_total"],
+                                        "sigma_mixed": repl["sigma_mixed"], "sigma_fp64": repl["sigma_fp64"],
+                                        "iterations": repl["iterations"]}
+        mixed_vs_fp64["refine_f32x2"] = {"solve_s": reports[-1]["seconds_total"],
+                                         "sigma_mixed": reports[-1]["sigma_mixed"],
+                                         "sigma_fp64": reports[-1]["sigma_fp64"],
+                                         "iterations": reports[-1]["iterations"]}
     B.sbd_destroy(handle)
 
     # end to end: pinned host inputs, eigenvector back to pinned host memory
@@ -619,7 +769,7 @@ def main():
             torch.distributed.barrier()
         t0 = time.perf_counter()
         n_sig_e2e = 0
-        for _ in range(args.steps):
+        for _ in range(min(args.steps, args.e2e_steps)):
             _, _, rep, _, _ = step(h_h, eri_h, A_h, B_h, vec_h)
             n_sig_e2e += rep["sigma_fp64"] + rep["sigma_mixed"]
         torch.cuda.synchronize()
@@ -627,7 +777,8 @@ def main():
         h2d = wl.h.nbytes + wl.eri.nbytes + wl.A.nbytes + wl.B.nbytes
         d2h = vec_h.numel() * 8 + wl.nroots * 8 * 2
         e2e = {"value": sum_over_ranks(float(wl.ndets) * n_sig_e2e, world) / te, "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "steps": min(args.steps, args.e2e_steps)}
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
@@ -635,6 +786,30 @@ def main():
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{nrows} sigma rows sampled uniformly from the {wl.ndets:.1e} determinants "
                          f"({dt:.1f} s); each row is one determinant's sigma element"}
+        if not args.no_oracle_extras:
+            cpu["extras"] = oracle_extras(rate, wl.ndets, cfg2_sigma_count=CFG2_FP64_SIGMA_COUNT,
+                                          full_cfg2=args.oracle_full)
+
+    # the batched and served forms (the engine) against the serial FP64 per-instance path, one GPU
+    legs = {}
+    if rank == 0 and world == 1 and args.legs:
+        want = {x.strip() for x in args.legs.split(",") if x.strip()}
+        if "batch" in want:
+            insts = W.batch_instances(64)[: args.leg_batch_n]
+            m = batch_measure(B, insts, args.engine_subspace, warmup=1, steps=1)
+            legs["batch"] = {"workload": f"the first {len(insts)} of the 64 batched instances (norb in "
+                                         f"{{16,20,24,26}}, |A|,|B| in [500,5000])",
+                             "engine_mixed": m["summary"], "serial_fp64": m["vs_serial_fp64"],
+                             "gpu_launches": int(m["stats"]["kernel_launches"])}
+        if "serve" in want:
+            traces, built, _ = serve_jobs(args.leg_requests, [args.rate], 5000)
+            m = serve_measure(B, built, traces, [args.rate], args.engine_subspace, int(args.budget_gb * 1e9), 5000,
+                              warmup=1)
+            legs["serve"] = {"workload": f"{args.leg_requests} Poisson arrivals at {args.rate:g}/s, norb in "
+                                         f"{{24,32,40,48,58}}, |A|=|B| log-uniform in [300,5000], "
+                                         f"{args.budget_gb:g} GB budget",
+                             "engine_mixed": m["serving"], "serial_fp64": m["vs_serial_fp64"],
+                             "gpu_launches": int(m["stats"]["kernel_launches"])}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -648,9 +823,8 @@ def main():
                 "sigma_only_dets_per_s": sigma_rate, "energy_Ha": float(energies[0]),
                 "residual": float(resid[0]),
                 # Kato-Temple-form estimate of the energy error: residual^2 / (next Ritz value - energy)
-                "energy_error_estimate_Ha": (float(resid[0]) ** 2 / reports[-1]["gap_estimate"]
-                                             if reports[-1].get("gap_estimate", 0.0) > 0.0 else None),
-                "kernels": kern, "mixed_vs_fp64": mixed_vs_fp64,
+                "energy_error_estimate_Ha": energy_error_estimates(energies, resid, reports[-1])[0],
+                "kernels": kern, "mixed_vs_fp64": mixed_vs_fp64, "engine_legs": legs or None,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk, "last_report": reports[-1]}
         print(json.dumps(line), flush=True)

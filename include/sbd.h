@@ -253,11 +253,15 @@ int64_t sbd_launch_count(void);
  *   bad_index_host NULL or one int64: -1, or for SBD_ERR_BAD_STRING the input
  *                position of a malformed string, for SBD_ERR_DUPLICATE_STRING the
  *                sorted position of a repeated string
- * Enqueued on `stream`, then synchronises it.  The first call on each device
- * looks up the work space's device address (cudaGetSymbolAddress) and caches
- * it; make that first call before any stream capture.  All calls share the
- * work space: calls that overlap on the GPU race and must be serialised by
- * the caller.  Errors are reported by sbd_last_error(NULL) on this thread.
+ * Every call is enqueued on `stream` and synchronises `stream` before it
+ * returns (the status words are read back).  The first call on each device
+ * looks up the work space's device address (cudaGetSymbolAddress, with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  The cached address assumes that the device's CUDA context lives
+ * as long as the library stays loaded (no cudaDeviceReset in between).  All
+ * calls share the work space: calls that overlap on the GPU race and must be
+ * serialised by the caller.  Errors are reported by sbd_last_error(NULL) on
+ * this thread.
  */
 #define SBD_NOALLOC_MAX_STRINGS 65536
 int sbd_sort_strings_noalloc(const uint64_t *keys_dev, int64_t n, int norb, int nel, uint64_t *sorted_dev,
@@ -369,6 +373,12 @@ typedef struct {
     sbd_alloc_fn alloc;      /* NULL: cudaMallocAsync / cudaFreeAsync */
     sbd_free_fn free;
     void *alloc_ctx;
+    /* Admission estimate of a job's excitation tables, in bytes per string (default 16384).  The
+     * estimate only decides when a job is tried: its handle is then created under the budget left
+     * after the running jobs and its own basis, and a job whose tables do not fit returns to the
+     * head of the queue until running jobs free memory (or fails with SBD_ERR_OVER_BUDGET when no
+     * other job holds memory). */
+    size_t table_bytes_per_string;
 } sbd_engine_options;
 
 typedef struct {
@@ -395,6 +405,7 @@ typedef struct {
     size_t bytes_in_use;      /* device bytes held for admitted jobs */
     size_t bytes_peak;
     int active, pending, done;
+    int64_t requeued;         /* admissions undone because a job's tables exceeded the budget left */
 } sbd_engine_stats;
 
 void sbd_engine_default_options(sbd_engine_options *opt);

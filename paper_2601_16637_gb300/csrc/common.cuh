@@ -34,6 +34,9 @@ constexpr int kPackJBits = 18;
 constexpr uint32_t kPackJMask = (1u << kPackJBits) - 1u;
 constexpr int kPackKeyShift = 18;  // pk >> 18 = 2*code + neg
 constexpr int64_t kMaxStringsPerSpin = (int64_t)1 << kPackJBits;
+constexpr int kSrcPairShift = 18;  // source-major singles: orbital-pair index at bits 18-28
+constexpr int kSrcNegBit = 29;     // and the phase at bit 29
+constexpr int kSrcItem = 8;        // source-major singles per work item
 constexpr int kBankGroups = 8;     // 16-byte bank groups of shared memory (32 banks x 4 bytes)
 constexpr int kListPad = 4;        // sigma lists are padded to multiples of 4 entries (16-byte loads)
 
@@ -76,6 +79,16 @@ struct SpinTables {
     uint2 *d_jv32 = nullptr;   // (d_j_sig, FP32 value bits), for the mixed sigma
     float2 *s_vx2 = nullptr;   // s_v64_sig as FP32 pairs (hi, lo), for the FP32-pair sigma
     float2 *d_vx2 = nullptr;   // d_v64_sig as FP32 pairs
+    // Source-major singles for the column-stationary alpha-beta pass.  The canonical singles list
+    // of each string is cut into items of at most kSrcItem entries (strings in ascending order,
+    // each string's items consecutive), so that the lanes of a warp, one item each, walk lists of
+    // nearly equal length; item t = string | entries << 18 (src_item[t]); entry i of item t is
+    // src_ent[(t / 32) * 32 * kSrcItem + 32 * i + t % 32] (coalesced for the 32 items of a warp):
+    // target (bits 0-17) | index of the unordered orbital pair {p, q} (bits 18-28) | phase -1 (bit 29).
+    uint32_t *src_item = nullptr;
+    uint32_t *src_ent = nullptr;
+    int64_t src_nitem = 0;
+    int src_maxdeg = 0;          // largest singles count of a string
     double *ediag = nullptr;     // [n] same-spin diagonal energies
     bool alias = false;          // storage owned by the other spin (A == B)
 };
@@ -91,6 +104,8 @@ struct Ctx {
     SpinTables sp[2];
     double *hd = nullptr;   // [N] Hamiltonian diagonal
     void *work_t = nullptr; // [N] doubles: transposed copy of one vector
+    float *rowmax = nullptr; // [nA] max |c(ia, :)| of the last mixed-precision vector (written by its beta pass)
+    float eri_absmax = 0.f;  // max |(pq|rs)| of the FP32 integrals
     size_t bytes_held = 0;
     std::vector<std::pair<void *, size_t>> allocs;
     std::string last_error;
@@ -203,6 +218,7 @@ struct BlockPlan {
     uint2 *d_jv32 = nullptr;
     float2 *d_vx2 = nullptr;
     void *work_t = nullptr;  // [nB][j1 - j0] doubles: the transposed source block
+    float *rowmax = nullptr; // [j1 - j0] max |c| of each source row (mixed alpha-beta pass)
     std::vector<void *> allocs;
 };
 BlockPlan *block_plan_create(Ctx &c, int64_t r0, int64_t r1, int64_t j0, int64_t j1);

@@ -585,6 +585,7 @@ struct sbd_engine_s {
     cudaGraphExec_t gA = nullptr, gB = nullptr;
     int64_t launches_A = 0, launches_B = 0;
     int64_t steps = 0, graph_launches = 0, kernel_launches = 0;
+    int64_t requeued = 0;  // admissions undone because the job's tables exceeded the budget left
     int grid_vec = 0;
     std::vector<SigmaSlot> s32, s64;
 
@@ -741,8 +742,9 @@ bool sbd_engine_s::admit_one()
     const int64_t nA = (int64_t)j->A.size(), nB = (int64_t)j->B.size();
     const int64_t N = nA * nB;
     // device bytes: basis and vectors, Hamiltonian diagonal + transposed work vector, and a
-    // reserve of 16 KB per string for the excitation tables
-    const size_t est = basis_bytes(N) + (size_t)N * 16 + (size_t)(nA + nB) * 16384;
+    // reserve per string for the excitation tables (an estimate: the handle's own allocations are
+    // held to the budget left after the basis when the job is created, below)
+    const size_t est = basis_bytes(N) + (size_t)N * 16 + (size_t)(nA + nB) * opt.table_bytes_per_string;
     if (opt.hbm_budget_bytes && bytes_in_use + est > opt.hbm_budget_bytes) {
         if (bytes_in_use == 0) {
             // cannot fit even alone: fail the job instead of blocking the queue
@@ -782,8 +784,20 @@ bool sbd_engine_s::admit_one()
         o.free = opt.free;
         o.alloc_ctx = opt.alloc_ctx;
         o.ecore = j->ecore;
+        // the tables, diagonal and work vectors of the handle (and whatever sbd_create holds while it
+        // runs) must fit what the budget leaves after the jobs in use and this job's basis
+        if (opt.hbm_budget_bytes) o.hbm_budget_bytes = opt.hbm_budget_bytes - bytes_in_use - basis_bytes(N);
         int rc = sbd_create(&s.handle, j->norb, j->na, j->nb, j->h.data(), j->eri.data(), j->A.data(), nA,
                             j->B.data(), nB, &o, (void *)stream);
+        if (rc == SBD_ERR_OVER_BUDGET && bytes_in_use > 0) {
+            // the estimate was too low: wait at the head of the queue until running jobs free memory
+            s = Slot{};
+            j->res.t_admit = 0.0;
+            j->res.ndets = 0;
+            pending.push_front(j);
+            requeued++;
+            return false;
+        }
         if (rc != SBD_OK) fail(rc, std::string("engine job: ") + sbd_last_error(nullptr));
         const Ctx &c = ctx_of(s.handle);
         if (std::max(c.nA, c.nB) > opt.max_strings || c.norb > opt.max_norb)
@@ -1209,6 +1223,7 @@ void sbd_engine_default_options(sbd_engine_options *o)
     o->max_strings = 20000;
     o->rows_per_item = 0;
     o->delta = 1e-4;
+    o->table_bytes_per_string = 16384;
 }
 
 int sbd_engine_create(sbd_engine *out, const sbd_engine_options *opt, void *stream)
@@ -1373,6 +1388,7 @@ int sbd_engine_get_stats(sbd_engine e, sbd_engine_stats *out)
     for (int i = 0; i < 3; ++i) out->tune_ms[i] = e->tune_ms[i];
     out->bytes_in_use = e->bytes_in_use;
     out->bytes_peak = e->bytes_peak;
+    out->requeued = e->requeued;
     for (const Slot &s : e->slots) out->active += s.job != nullptr;
     out->pending = (int)e->pending.size();
     for (const auto &kv : e->jobs) out->done += kv.second->finished;

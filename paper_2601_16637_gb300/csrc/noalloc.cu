@@ -33,7 +33,9 @@ void *g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the work space on the current device.  Host code only holds a
 // host-side stand-in under the array's name, so the address is looked up once per
-// device (with that device current) and cached.
+// device (with that device current) and cached.  The cache assumes that the device's
+// CUDA context lives as long as the library stays loaded: after a cudaDeviceReset the
+// cached address would name memory of the destroyed context.
 void *scratch_on_current_device()
 {
     int dev = 0;

@@ -244,6 +244,7 @@ BlockPlan *block_plan_create(Ctx &c, int64_t r0, int64_t r1, int64_t j0, int64_t
         }
         // transposed source block, doubles
         p->work_t = grab(sizeof(double) * (size_t)(j1 - j0) * (size_t)c.nB);
+        p->rowmax = (float *)grab(sizeof(float) * (size_t)(j1 - j0));
         SBD_CUDA(cudaStreamSynchronize(s));
     } catch (...) {
         block_plan_destroy(p);

@@ -33,6 +33,9 @@
 // of two floats, products are exact hi*hi (a fused multiply-add recovers the
 // rounding error, Dekker's product) plus the two cross terms, and sums use
 // Knuth's two-sum; on GB300 the FP32 pipe is ~64x the FP64 pipe).
+#include <string.h>
+
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -255,6 +258,7 @@ struct RowArgs {
     int accumulate;
     const double *hd;    // optional diagonal, indexed like Y
     const double *xd64;  // optional FP64 amplitudes [nrow][ncol] for the diagonal term
+    float *rowmax;       // optional (FP32 only): rowmax[r] = max_c |X[r][c]| of every row of the pass
     const uint64_t *row_strings;
     int norb;
     const double *eri;  // FP64 integrals, for the J vectors of the staged rows
@@ -281,12 +285,35 @@ __device__ __forceinline__ void row_group(const RowArgs<T> &a, int64_t r0, unsig
     {
         const int nr = (int)min((int64_t)R, a.nrow - r0);
         __syncthreads();
+        // row maxima (FP32 pass only): largest |x| as the bit pattern of a non-negative float, so a
+        // NaN amplitude leaves a NaN maximum
+        unsigned rmax[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) rmax[r] = 0u;
+        constexpr bool kMax = std::is_same<T, float>::value;
         if (STAGED) {
             for (int64_t c = tid; c < a.ncol; c += kThreads) {
                 T v[R];
 #pragma unroll
                 for (int r = 0; r < R; ++r) v[r] = r < nr ? conv<T>(a.X[(r0 + r) * a.ncol + c]) : T(0);
                 VecIO<T, R>::st(Xs + c * R, v);
+                if constexpr (kMax) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) rmax[r] = max(rmax[r], __float_as_uint(fabsf(v[r])));
+                }
+            }
+        } else if constexpr (kMax) {
+            if (a.rowmax)
+                for (int64_t c = tid; c < a.ncol; c += kThreads) rmax[0] = max(rmax[0], __float_as_uint(fabsf(a.X[r0 * a.ncol + c])));
+        }
+        __shared__ unsigned red_max[kMax ? R : 1][kMax ? kThreads / 32 : 1];
+        if constexpr (kMax) {
+            if (a.rowmax) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const unsigned w = __reduce_max_sync(0xffffffffu, rmax[r]);
+                    if (lane == 0) red_max[r][warp] = w;
+                }
             }
         }
         // sign-folded J table: row key = 2*code + neg holds (neg ? -1 : 1) * J_r[code]; code 0 rows
@@ -307,6 +334,13 @@ __device__ __forceinline__ void row_group(const RowArgs<T> &a, int64_t r0, unsig
             VecIO<T, R>::st(Js + (size_t)key * R, v);
         }
         __syncthreads();
+        if constexpr (kMax) {
+            if (a.rowmax && tid < nr) {
+                unsigned m = 0u;
+                for (int w = 0; w < kThreads / 32; ++w) m = max(m, red_max[tid][w]);
+                a.rowmax[r0 + tid] = __uint_as_float(m);
+            }
+        }
 
         int64_t cb = (int64_t)warp * kGroupsPerWarp;
         int64_t nxt_s0 = 0, nxt_s1 = 0, nxt_d0 = 0, nxt_d1 = 0;
@@ -550,15 +584,266 @@ __global__ void __launch_bounds__(Threads<T>::value) ab_pass_kernel(const AbArgs
     for (int64_t ia = blockIdx.x; ia < a.nA; ia += gridDim.x) ab_row<T, R, STAGED>(a, ia, smem);
 }
 
-// out[c][r] = in[r][c]
+// ---------------------------------------------------------------------------
+// Column-stationary alpha-beta pass of the mixed sigma.
+//
+// For output row ia with alpha singles (ja_k, pq_k, u_k), k < K, and the beta singles of each
+// string (ib <- jb with orbital pair {r, s}, phase t; by Hermiticity the singles list of jb names
+// every ib that has jb among its singles, with the same phase):
+//   s(ia, ib) += sum_{jb} sum_{ib in singles(jb)} t * sum_k W[{r,s}][k] C(ja_k, jb),
+//   W[{r,s}][k] = u_k (p_k q_k|rs)                       ((pq|rs) = (pq|sr) for real orbitals)
+// The alpha singles are taken in chunks of KC <= 32.  A lane owns one column jb: it holds the KC
+// amplitudes C(ja_k, jb) in registers and walks the singles of jb; for each it gathers one
+// 4*KC-byte row of W from shared memory (the only shared-memory operand of the multiply-adds,
+// 4 bytes per FMA) and adds the FP32 dot product to the row accumulator of ib.
+//
+// Bank conflicts: a W row is 128 bytes (eight 16-byte chunks).  With KC = 32 lane l reads chunk
+// (step + l) mod 8 at each step, so the 8 lanes of a 128-bit phase hit 8 distinct bank groups
+// whatever rows they read; with KC = 16 (8) each row holds 2 (4) copies and lanes read their own
+// copy, rotated within it.  The lane's registers hold the amplitudes in the same rotated order.
+//
+// Determinism: the row accumulator holds 64-bit fixed-point integers with one scale per output row,
+// 2^e with e chosen so that the largest possible row sum,
+//   maxdeg_beta * max|(pq|rs)| * sum_k max_jb |C(ja_k, jb)|,
+// stays below 2^60; each FP32 dot product is rounded once onto that grid and integer addition is
+// exact and order independent, so the result does not depend on the order of the shared-memory
+// atomics.  The grid step is at most 2^-59 of that bound, far below FP32 rounding of the products.
+// The accumulated row is added to s(ia, :) in FP64 by the CTA that owns the row.
+
+constexpr int kSrcThreads = 1024;
+
+struct AbSrcArgs {
+    const float *C;  // [nA][nB] FP32 amplitudes
+    double *S;       // [nA][nB], accumulated
+    int64_t nA, nB;
+    int norb, npair;
+    const float *eri;         // FP32 (pq|rs) as [norb^2][norb^2]
+    const int64_t *as_ptr;    // alpha singles, canonical CSR
+    const uint32_t *as_pk;
+    const uint32_t *src_item; // beta singles, source-major items (string | entries << 18)
+    const uint32_t *src_ent;
+    int64_t src_nitem;
+    const float *rowmax;      // [nA] max |C(ja, :)|
+    float bound;              // maxdeg_beta * max |(pq|rs)|
+};
+
+// shared memory of one CTA: W [npair][8] float4, accumulator [nB] u64, pair -> rs code
+__host__ __device__ constexpr size_t src_w_bytes(int npair) { return (size_t)npair * 128; }
+__host__ __device__ inline size_t src_smem(int npair, int64_t nB)
+{
+    return src_w_bytes(npair) + (size_t)nB * 8 + round16((size_t)npair * 2);
+}
+
+template <int KC>
+__device__ __forceinline__ void src_chunk(const AbSrcArgs &a, const float4 *__restrict__ Wt,
+                                          unsigned long long *acc, const int *ja_s, int kc, float scale,
+                                          int *ctr)
+{
+    constexpr int CPW = KC / 4;  // 16-byte chunks per copy of a W row
+    const int lane = threadIdx.x & 31;
+    const int rot = lane & (CPW - 1);
+    const int base = ((lane / CPW) & (8 / CPW - 1)) * CPW;  // first chunk of this lane's copy
+    const int nsl = (int)((a.src_nitem + 31) >> 5);
+    while (true) {
+        int sl = 0;
+        if (lane == 0) sl = atomicAdd(ctr, 1);
+        sl = __shfl_sync(0xffffffffu, sl, 0);
+        if (sl >= nsl) break;
+        // one item per lane: a string jb (column of C) and at most kSrcItem of its singles
+        const int64_t t = (int64_t)sl * 32 + lane;
+        const uint32_t info = t < a.src_nitem ? __ldg(a.src_item + t) : 0u;
+        const int64_t jb = info & kPackJMask;
+        const int cnt = (int)(info >> kSrcPairShift);
+        const uint32_t *ent = a.src_ent + (int64_t)sl * 32 * kSrcItem + lane;
+        uint32_t e[kSrcItem];
+#pragma unroll
+        for (int i = 0; i < kSrcItem; ++i) e[i] = i < cnt ? __ldg(ent + 32 * i) : 0u;
+        // amplitudes of the chunk's alpha singles at column jb (consecutive lanes: consecutive or equal
+        // columns), then rotated by `rot` chunks so that register chunk s holds amplitude chunk
+        // (s + rot) mod CPW
+        float cv[KC];
+#pragma unroll
+        for (int k4 = 0; k4 < KC; k4 += 4) {
+            const int4 j4 = *reinterpret_cast<const int4 *>(ja_s + k4);  // one broadcast load per 4 rows
+            const int jr[4] = {j4.x, j4.y, j4.z, j4.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                cv[k4 + i] = (cnt > 0 && k4 + i < kc) ? __ldg(a.C + (int64_t)jr[i] * a.nB + jb) : 0.f;
+        }
+#pragma unroll
+        for (int b = 1; b < CPW; b <<= 1) {
+            if (rot & b) {
+                float tmp[KC];
+#pragma unroll
+                for (int s = 0; s < CPW; ++s)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) tmp[4 * s + i] = cv[4 * ((s + b) % CPW) + i];
+#pragma unroll
+                for (int k = 0; k < KC; ++k) cv[k] = tmp[k];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kSrcItem; i += 2) {  // two singles per round for independent chains
+            if (i < cnt) {
+                const bool two = i + 1 < cnt;
+                const float4 *w0 = Wt + ((e[i] >> kSrcPairShift) & 0x7ffu) * 8 + base;
+                const float4 *w1 = Wt + ((e[i + 1] >> kSrcPairShift) & 0x7ffu) * 8 + base;
+                float f0 = 0.f, f1 = 0.f;
+#pragma unroll
+                for (int s = 0; s < CPW; ++s) {
+                    const int q = (s + rot) & (CPW - 1);
+                    const float4 x0 = w0[q];
+                    const float4 x1 = two ? w1[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    f0 = fmaf(x0.x, cv[4 * s], f0);
+                    f1 = fmaf(x1.x, cv[4 * s], f1);
+                    f0 = fmaf(x0.y, cv[4 * s + 1], f0);
+                    f1 = fmaf(x1.y, cv[4 * s + 1], f1);
+                    f0 = fmaf(x0.z, cv[4 * s + 2], f0);
+                    f1 = fmaf(x1.z, cv[4 * s + 2], f1);
+                    f0 = fmaf(x0.w, cv[4 * s + 3], f0);
+                    f1 = fmaf(x1.w, cv[4 * s + 3], f1);
+                }
+                long long v0 = __float2ll_rn(f0 * scale);
+                if ((e[i] >> kSrcNegBit) & 1u) v0 = -v0;
+                atomicAdd(acc + (e[i] & kPackJMask), (unsigned long long)v0);
+                if (two) {
+                    long long v1 = __float2ll_rn(f1 * scale);
+                    if ((e[i + 1] >> kSrcNegBit) & 1u) v1 = -v1;
+                    atomicAdd(acc + (e[i + 1] & kPackJMask), (unsigned long long)v1);
+                }
+            }
+        }
+    }
+}
+
+// W[x][position p] for the chunk's alpha singles, position p holding amplitude chunk p mod CPW
+template <int KC>
+__device__ __forceinline__ void src_build_w(const AbSrcArgs &a, float4 *Wt, const int16_t *rs_of,
+                                            const int *pq_s, const float *u_s, int kc)
+{
+    constexpr int CPW = KC / 4;
+    const int n2 = a.norb * a.norb;
+    for (int idx = threadIdx.x; idx < a.npair * 8; idx += blockDim.x) {
+        const int p = idx / a.npair, x = idx - p * a.npair;
+        const int c = p & (CPW - 1);
+        const int rs = rs_of[x];
+        float v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = 4 * c + i;
+            v[i] = k < kc ? u_s[k] * __ldg(a.eri + (size_t)pq_s[k] * n2 + rs) : 0.f;
+        }
+        Wt[(size_t)x * 8 + p] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
+__device__ __forceinline__ void src_row(const AbSrcArgs &a, int64_t ia, unsigned char *smem)
+{
+    float4 *Wt = reinterpret_cast<float4 *>(smem);
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(smem + src_w_bytes(a.npair));
+    const int16_t *rs_of = reinterpret_cast<const int16_t *>(smem + src_w_bytes(a.npair) + (size_t)a.nB * 8);
+    __shared__ __align__(16) int ja_s[32];
+    __shared__ int pq_s[32];
+    __shared__ float u_s[32];
+    __shared__ int ctr;
+    __shared__ float s_scale;
+    __shared__ double s_inv;
+    __shared__ int s_state;  // 0 skip the row, 1 accumulate, 2 non-finite amplitudes
+    const int tid = threadIdx.x;
+    const int64_t e0 = a.as_ptr[ia];
+    const int K = (int)(a.as_ptr[ia + 1] - e0);
+    __syncthreads();  // the previous row is finished with shared memory
+    for (int64_t ib = tid; ib < a.nB; ib += blockDim.x) acc[ib] = 0ull;
+    {
+        int16_t *rs_w = reinterpret_cast<int16_t *>(smem + src_w_bytes(a.npair) + (size_t)a.nB * 8);
+        for (int r = 1; r < a.norb; ++r)
+            for (int s = tid; s < r; s += blockDim.x) rs_w[r * (r - 1) / 2 + s] = (int16_t)(r * a.norb + s);
+    }
+    if (tid < 32) {
+        float m = 0.f;
+        for (int k = tid; k < K; k += 32) m += __ldg(a.rowmax + (a.as_pk[e0 + k] & kPackJMask));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) m += __shfl_xor_sync(0xffffffffu, m, off);
+        if (tid == 0) {
+            const double bnd = (double)m * (double)a.bound;
+            if (!(bnd <= 1e300)) {
+                s_state = 2;
+            } else if (bnd == 0.0) {
+                s_state = 0;
+            } else {
+                int e = 60 - ilogb(bnd) - 1;  // bnd < 2^(ilogb+1), so bnd * 2^e < 2^60
+                e = max(-120, min(120, e));
+                s_scale = ldexpf(1.f, e);
+                s_inv = ldexp(1.0, -e);
+                s_state = 1;
+            }
+        }
+    }
+    __syncthreads();
+    const int state = s_state;
+    if (state == 0) return;
+    if (state == 2) {
+        for (int64_t ib = tid; ib < a.nB; ib += blockDim.x) a.S[ia * a.nB + ib] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    const float scale = s_scale;
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        const int kc = min(32, K - k0);
+        __syncthreads();  // the previous chunk is finished with W and the chunk arrays
+        if (tid < kc) {
+            const uint32_t pk = a.as_pk[e0 + k0 + tid];
+            ja_s[tid] = (int)(pk & kPackJMask);
+            pq_s[tid] = (int)(pk >> (kPackKeyShift + 1));
+            u_s[tid] = ((pk >> kPackKeyShift) & 1u) ? -1.f : 1.f;
+        }
+        if (tid == 0) ctr = 0;
+        __syncthreads();
+        if (kc <= 8) {
+            src_build_w<8>(a, Wt, rs_of, pq_s, u_s, kc);
+            __syncthreads();
+            src_chunk<8>(a, Wt, acc, ja_s, kc, scale, &ctr);
+        } else if (kc <= 16) {
+            src_build_w<16>(a, Wt, rs_of, pq_s, u_s, kc);
+            __syncthreads();
+            src_chunk<16>(a, Wt, acc, ja_s, kc, scale, &ctr);
+        } else {
+            src_build_w<32>(a, Wt, rs_of, pq_s, u_s, kc);
+            __syncthreads();
+            src_chunk<32>(a, Wt, acc, ja_s, kc, scale, &ctr);
+        }
+    }
+    __syncthreads();
+    const double inv = s_inv;
+    for (int64_t ib = tid; ib < a.nB; ib += blockDim.x) a.S[ia * a.nB + ib] += (double)(long long)acc[ib] * inv;
+}
+
+__global__ void __launch_bounds__(kSrcThreads, 1) ab_src_kernel(const AbSrcArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int64_t ia = blockIdx.x; ia < a.nA; ia += gridDim.x) src_row(a, ia, smem);
+}
+
+// out[c][r] = in[r][c]; with rowmax (FP32 only, zeroed beforehand): rowmax[r] = max_c |in[r][c]|,
+// accumulated as the bit patterns of non-negative floats (a NaN row stays NaN)
 template <typename T>
-__global__ void transpose_kernel(const T *__restrict__ in, T *__restrict__ out, int64_t rows, int64_t cols)
+__global__ void transpose_kernel(const T *__restrict__ in, T *__restrict__ out, int64_t rows, int64_t cols,
+                                 float *rowmax = nullptr)
 {
     __shared__ T tile[32][33];
     const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
     for (int j = threadIdx.y; j < 32; j += 8) {
         const int64_t r = by + j, c = bx + threadIdx.x;
-        if (r < rows && c < cols) tile[j][threadIdx.x] = in[r * cols + c];
+        T v = T(0);
+        if (r < rows && c < cols) {
+            v = in[r * cols + c];
+            tile[j][threadIdx.x] = v;
+        }
+        if constexpr (sizeof(T) == 4) {
+            if (rowmax) {  // uniform per launch
+                const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf((float)v)));
+                if (threadIdx.x == 0 && r < rows) atomicMax(reinterpret_cast<unsigned *>(rowmax) + r, m);
+            }
+        }
     }
     __syncthreads();
     for (int j = threadIdx.y; j < 32; j += 8) {
@@ -592,6 +877,52 @@ PassCfg choose(int64_t ncol, int n2, size_t elem, int rmax, size_t limit)
 }
 
 size_t smem_limit(const Ctx &c) { return (size_t)c.smem_optin - 1024; }
+
+// max |x| over n floats, as the bit pattern of a non-negative float (out zeroed beforehand)
+__global__ void absmax_kernel(const float *__restrict__ x, int64_t n, unsigned *out)
+{
+    unsigned m = 0u;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, __float_as_uint(fabsf(x[i])));
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+int npairs(int norb) { return norb * (norb - 1) / 2; }
+
+// the column-stationary alpha-beta pass applies when its W table and row accumulator fit
+bool src_fits(const Ctx &c)
+{
+    return c.norb >= 2 && c.sp[1].src_ent && src_smem(npairs(c.norb), c.nB) <= smem_limit(c);
+}
+
+AbSrcArgs src_args(const Ctx &c, const float *C, double *S, const float *rowmax)
+{
+    const SpinTables &ta = c.sp[0], &tb = c.sp[1];
+    AbSrcArgs a{};
+    a.C = C;
+    a.S = S;
+    a.nA = c.nA;
+    a.nB = c.nB;
+    a.norb = c.norb;
+    a.npair = npairs(c.norb);
+    a.eri = c.eri32;
+    a.as_ptr = ta.s_ptr;
+    a.as_pk = ta.s_pk;
+    a.src_item = tb.src_item;
+    a.src_ent = tb.src_ent;
+    a.src_nitem = tb.src_nitem;
+    a.rowmax = rowmax;
+    a.bound = (float)((double)tb.src_maxdeg * (double)c.eri_absmax);
+    return a;
+}
+
+void launch_ab_src(const AbSrcArgs &a, int num_sms, cudaStream_t s)
+{
+    const int grid = (int)std::min<int64_t>(a.nA, (int64_t)num_sms);
+    ab_src_kernel<<<grid, kSrcThreads, src_smem(a.npair, a.nB), s>>>(a);
+    SBD_LAUNCH("ab_src_kernel");
+}
 
 template <typename T>
 void set_attrs(int optin)
@@ -634,12 +965,13 @@ void launch_ab(const AbArgs<T> &a, const PassCfg &p, cudaStream_t s)
 }
 
 template <typename T>
-void transpose(const T *in, T *out, int64_t rows, int64_t cols, cudaStream_t s)
+void transpose(const T *in, T *out, int64_t rows, int64_t cols, cudaStream_t s, float *rowmax = nullptr)
 {
     const int64_t gy = (rows + 31) / 32;
     if (gy > 65535) fail(SBD_ERR_UNSUPPORTED, "alpha string set too large for the transpose");
     dim3 grid((unsigned)((cols + 31) / 32), (unsigned)gy);
-    transpose_kernel<T><<<grid, dim3(32, 8), 0, s>>>(in, out, rows, cols);
+    if (rowmax) SBD_CUDA(cudaMemsetAsync(rowmax, 0, (size_t)rows * sizeof(float), s));
+    transpose_kernel<T><<<grid, dim3(32, 8), 0, s>>>(in, out, rows, cols, rowmax);
     SBD_LAUNCH("transpose_kernel");
 }
 
@@ -746,12 +1078,21 @@ void apply(Ctx &c, const typename In<T>::type *C, double *S, const double *c64, 
     const size_t lim = smem_limit(c);
     const int base = kSlotBase<T>;
     E *Ct = static_cast<E *>(c.work_t);
+    // the mixed alpha-beta pass takes the row maxima of C from the beta pass
+    const bool src = std::is_same<T, float>::value && src_fits(c);
     timed(c, base + 0, s, [&] { transpose<E>(C, Ct, c.nA, c.nB, s); });
     RowArgs<T> rb, ra;
     AbArgs<T> ab;
     make_args<T>(c, C, S, c64, Ct, rb, ra, ab);
+    if (src) rb.rowmax = c.rowmax;
     timed(c, base + 1, s, [&] { launch_row<T>(rb, choose(c.nB, n2, sizeof(T), rmax, lim), s); });
     timed(c, base + 2, s, [&] { launch_row<T>(ra, choose(c.nA, n2, sizeof(T), rmax, lim), s); });
+    if constexpr (std::is_same<T, float>::value) {
+        if (src) {
+            timed(c, base + 3, s, [&] { launch_ab_src(src_args(c, C, S, c.rowmax), c.num_sms, s); });
+            return;
+        }
+    }
     timed(c, base + 3, s, [&] { launch_ab<T>(ab, choose(c.nB, n2, sizeof(T), rmax, lim), s); });
 }
 
@@ -769,7 +1110,7 @@ struct TDesc {
 };
 
 struct Layout {
-    size_t n, off_t, off_b, off_a, off_ab, td, rb, ra, ab, total;
+    size_t n, off_t, off_b, off_a, off_ab, td, rb, ra, ab, src, total;
 };
 
 template <typename T>
@@ -791,6 +1132,7 @@ Layout layout_for(int m)
     L.rb = take(sizeof(RowArgs<T>) * m);
     L.ra = take(sizeof(RowArgs<T>) * m);
     L.ab = take(sizeof(AbArgs<T>) * m);
+    L.src = take(sizeof(AbSrcArgs) * m);
     L.total = o;
     return L;
 }
@@ -884,6 +1226,15 @@ __global__ void __launch_bounds__(Threads<T>::value) ab_batch_kernel(const int *
     item_loop(pn, off, args, counter, sa, [&](int64_t li) { ab_row<T, R, true>(sa, li, smem); });
 }
 
+__global__ void __launch_bounds__(kSrcThreads, 1) ab_src_batch_kernel(const int *pn, const int64_t *off,
+                                                                      const AbSrcArgs *args,
+                                                                      unsigned long long *counter)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ AbSrcArgs sa;
+    item_loop(pn, off, args, counter, sa, [&](int64_t li) { src_row(sa, li, smem); });
+}
+
 size_t batch_smem(size_t elem, int R, int max_strings, int max_norb)
 {
     return round16((size_t)max_strings * R * elem) + (size_t)2 * max_norb * max_norb * R * elem;
@@ -893,8 +1244,10 @@ size_t batch_smem(size_t elem, int R, int max_strings, int max_norb)
 
 struct SigmaBatch {
     sbd_precision prec = SBD_MIXED;
-    int max_slots = 0, R = 1, device = 0, grid_pass = 0, grid_t = 0;
+    int max_slots = 0, R = 1, device = 0, grid_pass = 0, grid_t = 0, grid_src = 0;
     size_t smem = 0;
+    bool src = false;     // mixed: the column-stationary alpha-beta pass (when its table and accumulator fit)
+    size_t src_smem = 0;
     Layout L{};
     unsigned char *dev = nullptr, *host = nullptr;
     unsigned long long *counters = nullptr;  // [3]: beta, alpha, alpha-beta
@@ -921,6 +1274,12 @@ void batch_set(SigmaBatch *b, const SigmaSlot *slots, int n)
         const E *x = static_cast<const E *>(sl.x);
         E *xt = static_cast<E *>(sl.xt);
         make_args<T>(c, x, sl.y, sl.x64, xt, rb[i], ra[i], ab[i]);
+        if constexpr (std::is_same<T, float>::value) {
+            if (b->src) {
+                rb[i].rowmax = c.rowmax;
+                reinterpret_cast<AbSrcArgs *>(h + L.src)[i] = src_args(c, x, sl.y, c.rowmax);
+            }
+        }
         td[i] = TDesc<E>{x, xt, c.nA, c.nB};
         ot[i + 1] = ot[i] + ((c.nA + 31) / 32) * ((c.nB + 31) / 32);
         ob[i + 1] = ob[i] + (c.nA + b->R - 1) / b->R;
@@ -947,6 +1306,13 @@ void batch_launch_r(SigmaBatch *b, cudaStream_t s)
         pn, reinterpret_cast<const int64_t *>(d + L.off_a), reinterpret_cast<const RowArgs<T> *>(d + L.ra),
         b->counters + 1);
     SBD_LAUNCH("row_batch_kernel");
+    if (std::is_same<T, float>::value && b->src) {
+        ab_src_batch_kernel<<<b->grid_src, kSrcThreads, b->src_smem, s>>>(
+            pn, reinterpret_cast<const int64_t *>(d + L.off_ab), reinterpret_cast<const AbSrcArgs *>(d + L.src),
+            b->counters + 2);
+        SBD_LAUNCH("ab_src_batch_kernel");
+        return;
+    }
     ab_batch_kernel<T, R><<<b->grid_pass, kThreads, b->smem, s>>>(
         pn, reinterpret_cast<const int64_t *>(d + L.off_ab), reinterpret_cast<const AbArgs<T> *>(d + L.ab),
         b->counters + 2);
@@ -967,15 +1333,37 @@ void batch_attrs(SigmaBatch *b)
     SBD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
     b->grid_pass = sms * occ;
     b->grid_t = sms * 8;
+    if (b->src) {
+        SBD_CUDA(cudaFuncSetAttribute(ab_src_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)b->src_smem));
+        int occ_src = 0;
+        SBD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_src, ab_src_batch_kernel, kSrcThreads, b->src_smem));
+        b->grid_src = sms * std::max(1, occ_src);
+    }
 }
 
 }  // namespace
 
 void sigma_prepare(Ctx &c)
 {
-    set_attrs<double>(c.smem_optin);
-    set_attrs<float>(c.smem_optin);
-    set_attrs<F2>(c.smem_optin);
+    // dynamic shared memory up to smem_limit(): the kernels' static shared memory (at most 1 KB) and
+    // the dynamic part must stay within the opt-in maximum together
+    const int lim = (int)smem_limit(c);
+    set_attrs<double>(lim);
+    set_attrs<float>(lim);
+    set_attrs<F2>(lim);
+    SBD_CUDA(cudaFuncSetAttribute(ab_src_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    // max |(pq|rs)| of the FP32 integrals, for the fixed-point scale of the alpha-beta pass
+    const int64_t n4 = (int64_t)c.norb * c.norb * c.norb * c.norb;
+    unsigned *m = reinterpret_cast<unsigned *>(c.dstat);  // status words are free after create
+    SBD_CUDA(cudaMemsetAsync(m, 0, sizeof(unsigned), c.stream));
+    absmax_kernel<<<(int)std::min<int64_t>((n4 + 255) / 256, 1024), 256, 0, c.stream>>>(c.eri32, n4, m);
+    SBD_LAUNCH("absmax_kernel");
+    unsigned bits = 0;
+    SBD_CUDA(cudaMemcpyAsync(&bits, m, sizeof(unsigned), cudaMemcpyDeviceToHost, c.stream));
+    SBD_CUDA(cudaStreamSynchronize(c.stream));
+    memcpy(&c.eri_absmax, &bits, sizeof(float));
+    c.rowmax = dalloc_n<float>(c, (size_t)c.nA);
 }
 
 size_t sigma_batch_smem(sbd_precision prec, int R, int max_strings, int max_norb)
@@ -1004,6 +1392,8 @@ SigmaBatch *sigma_batch_create(int max_slots, sbd_precision prec, int R, int max
     b->R = R;
     b->device = device;
     b->smem = smem;
+    b->src_smem = src_smem(npairs(max_norb), max_strings);
+    b->src = prec == SBD_MIXED && max_norb >= 2 && b->src_smem <= sigma_batch_smem_limit(device);
     b->L = prec == SBD_FP64 ? layout_for<double>(max_slots)
                             : (prec == SBD_F32X2 ? layout_for<F2>(max_slots) : layout_for<float>(max_slots));
     try {
@@ -1084,7 +1474,9 @@ void apply_block(BlockPlan &p, const typename In<T>::type *Cb, double *S, cudaSt
     const int64_t nj = p.j1 - p.j0, nr = p.r1 - p.r0;
     const SpinTables &ta = c.sp[0], &tb = c.sp[1];
     E *Ct = static_cast<E *>(p.work_t);
-    transpose<E>(Cb, Ct, nj, c.nB, s);
+    // mixed: the column-stationary alpha-beta pass takes the source rows' maxima from the transpose
+    const bool src = std::is_same<T, float>::value && src_fits(c);
+    transpose<E>(Cb, Ct, nj, c.nB, s, src ? p.rowmax : nullptr);
     // beta pass: the output rows inside the block
     const int64_t lo = std::max(p.r0, p.j0), hi = std::min(p.r1, p.j1);
     RowArgs<T> rb, ra;
@@ -1117,6 +1509,16 @@ void apply_block(BlockPlan &p, const typename In<T>::type *Cb, double *S, cudaSt
     else ra.lists = Lists<double>{p.s_pk_sig, p.s_v64_sig, p.d_j_sig, p.d_v64_sig};
     launch_row<T>(ra, choose(nj, n2, sizeof(T), rmax, lim), s);
     // alpha-beta pass: output rows r0..r1, their alpha singles inside the block
+    if constexpr (std::is_same<T, float>::value) {
+        if (src) {
+            AbSrcArgs a = src_args(c, Cb, S, p.rowmax);
+            a.nA = nr;
+            a.as_ptr = p.s_ptr;
+            a.as_pk = p.s_pk;
+            launch_ab_src(a, c.num_sms, s);
+            return;
+        }
+    }
     ab.C = Cb;
     ab.S = S;
     ab.nA = nr;

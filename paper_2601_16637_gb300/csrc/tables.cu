@@ -460,6 +460,40 @@ __global__ void padded_count_kernel(const int64_t *__restrict__ ptr, int64_t n, 
     }
 }
 
+// Source-major singles (column-stationary alpha-beta pass): cnt[i] = items of string i (its singles
+// in pieces of kSrcItem); *maxdeg = largest singles count.
+__global__ void src_count_kernel(const int64_t *__restrict__ ptr, int64_t n, int64_t *cnt, int *maxdeg)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (int)(ptr[i + 1] - ptr[i]);
+        cnt[i] = (d + kSrcItem - 1) / kSrcItem;
+        atomicMax(maxdeg, d);
+    }
+}
+
+// items of string i from item ioff[i] on; each entry keeps the target and phase of the canonical
+// single and replaces its orbital code p*norb+q by the index r(r-1)/2 + s of the pair r = max, s = min
+__global__ void src_fill_kernel(const int64_t *__restrict__ ptr, const uint32_t *__restrict__ pk, int64_t n,
+                                int norb, const int64_t *__restrict__ ioff, uint32_t *item, uint32_t *ent)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = ptr[i], e = ptr[i + 1];
+        for (int64_t x = b; x < e; ++x) {
+            const int64_t t = ioff[i] + (x - b) / kSrcItem;
+            const int slot = (int)((x - b) % kSrcItem);
+            if (slot == 0) item[t] = (uint32_t)i | ((uint32_t)min((int64_t)kSrcItem, e - x) << kSrcPairShift);
+            const uint32_t v = pk[x];
+            const int code = (int)(v >> (kPackKeyShift + 1));
+            const int p = code / norb, q = code - p * norb;
+            const int r = max(p, q), s = min(p, q);
+            const uint32_t pair = (uint32_t)(r * (r - 1) / 2 + s);
+            const uint32_t neg = (v >> kPackKeyShift) & 1u;
+            ent[(t / 32) * 32 * kSrcItem + 32 * slot + (t % 32)] =
+                (v & kPackJMask) | (pair << kSrcPairShift) | (neg << kSrcNegBit);
+        }
+    }
+}
+
 // (key, FP32 value) pairs for single 8-byte loads in the mixed sigma
 __global__ void pair_kernel(const uint32_t *__restrict__ key, const double *__restrict__ val, uint2 *out, int64_t n)
 {
@@ -649,6 +683,28 @@ void build_tables(Ctx &c, int spin)
         SBD_LAUNCH("split_kernel(doubles)");
     }
     dfree(c, perm);
+    // source-major singles: items of at most kSrcItem singles, 32 items per slice
+    {
+        int64_t *ioff = dalloc_n<int64_t>(c, n + 1);
+        int *dmax = reinterpret_cast<int *>(cnt + n);  // the doubles counts are no longer needed
+        SBD_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), c.stream));
+        src_count_kernel<<<blocks_for(n, 256), 256, 0, c.stream>>>(t.s_ptr, n, cnt, dmax);
+        SBD_LAUNCH("src_count_kernel");
+        scan_kernel<<<1, 1024, 0, c.stream>>>(cnt, n, ioff);
+        SBD_LAUNCH("scan_kernel(source-major singles)");
+        SBD_CUDA(cudaMemcpyAsync(&t.src_nitem, ioff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, c.stream));
+        SBD_CUDA(cudaMemcpyAsync(&t.src_maxdeg, dmax, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+        SBD_CUDA(cudaStreamSynchronize(c.stream));
+        const int64_t nsl = std::max<int64_t>((t.src_nitem + 31) / 32, 1);
+        t.src_item = dalloc_n<uint32_t>(c, (size_t)nsl * 32);
+        t.src_ent = dalloc_n<uint32_t>(c, (size_t)nsl * 32 * kSrcItem);
+        SBD_CUDA(cudaMemsetAsync(t.src_item, 0, (size_t)nsl * 32 * sizeof(uint32_t), c.stream));
+        SBD_CUDA(cudaMemsetAsync(t.src_ent, 0, (size_t)nsl * 32 * kSrcItem * sizeof(uint32_t), c.stream));
+        src_fill_kernel<<<blocks_for(n, 128), 128, 0, c.stream>>>(t.s_ptr, t.s_pk, n, norb, ioff, t.src_item,
+                                                                  t.src_ent);
+        SBD_LAUNCH("src_fill_kernel");
+        dfree(c, ioff);
+    }
     t.ediag = dalloc_n<double>(c, n);
     ediag_kernel<<<blocks_for(n, 128), 128, 0, c.stream>>>(t.strings, n, norb, c.h64, c.eri64, t.ediag);
     SBD_LAUNCH("ediag_kernel");

@@ -80,14 +80,29 @@ class RingSigma:
 
 def device_block_sigma(handle, bounds: Sequence[int], rank: int, precision, stream=None):
     """block_sigma for RingSigma on a GPU: one block plan per source block (sbd_block_plan_create),
-    products by sbd_sigma_block.  Returns (callable, close)."""
+    products by sbd_sigma_block.  Returns (callable, close).
+
+    RingSigma orders its own device work (zeroing the rows, the NCCL receives it waits for) on
+    torch's current stream.  With stream=None the products run there too.  A torch.cuda.Stream
+    given here first waits for everything queued on the current stream, and the current stream
+    then waits for the product, so a block is never read before it has arrived, rows are never
+    added to before they are zeroed, and a receive buffer is not overwritten while a product still
+    reads it."""
     from . import binding as B
 
     r0, r1 = bounds[rank], bounds[rank + 1]
     plans = [B.sbd_block_plan_create(handle, r0, r1, bounds[b], bounds[b + 1]) for b in range(len(bounds) - 1)]
 
     def block_sigma(b, c_block, out_rows):
+        import torch
+
+        cur = torch.cuda.current_stream()
+        if stream is None or stream == cur:
+            B.sbd_sigma_block(plans[b], c_block, out_rows, precision, cur)
+            return
+        stream.wait_stream(cur)
         B.sbd_sigma_block(plans[b], c_block, out_rows, precision, stream)
+        cur.wait_stream(stream)
 
     def close():
         for p in plans:

@@ -42,3 +42,31 @@ def test_traffic_record_matches_only_the_current_kernel_source():
     else:
         assert got is None  # a record taken on other kernel source is not reported
     assert bench.traffic_record("no_such_kernel") is None
+
+
+def test_nvidia_smi_is_given_the_device_this_process_uses():
+    import uuid
+
+    class Props:
+        pass
+
+    p = Props()
+    # CUDA_VISIBLE_DEVICES remaps: CUDA device 1 of this process is physical GPU 5
+    assert bench.nvsmi_gpu_id(1, props=p, visible="3,5") == "5"
+    assert bench.nvsmi_gpu_id(0, props=p, visible="GPU-aaaa,GPU-bbbb") == "GPU-aaaa"
+    assert bench.nvsmi_gpu_id(0, props=p, visible="") == "0"
+    # with a UUID the device is named by it, whatever CUDA_VISIBLE_DEVICES says
+    u = uuid.UUID("12345678-1234-5678-1234-567812345678")
+    p.uuid = u
+    assert bench.nvsmi_gpu_id(1, props=p, visible="3,5") == "GPU-" + str(u)
+
+
+def test_energy_error_estimate_uses_the_distance_to_the_next_ritz_value():
+    # three roots; the first Ritz value above them lies gap = 0.5 above the third
+    e = [-2.0, -1.5, -1.25]
+    r = [1e-4, 2e-4, 3e-4]
+    est = bench.energy_error_estimates(e, r, {"gap_estimate": 0.5})
+    assert abs(est[0] - 1e-8 / (0.5 + 0.75)) < 1e-20
+    assert abs(est[1] - 4e-8 / (0.5 + 0.25)) < 1e-20
+    assert abs(est[2] - 9e-8 / 0.5) < 1e-20
+    assert bench.energy_error_estimates(e, r, {"gap_estimate": 0.0}) == [None, None, None]

@@ -180,6 +180,38 @@ def test_engine_budget_admission_and_jobs_joining_a_running_batch(B, alone):
         assert a["t_done"] <= b["t_admit"] or b["t_done"] <= a["t_admit"]
 
 
+def _basis(wl, max_sub=12):
+    # the engine's per-job vectors: V, W [max_sub][N], U, HU, TC in FP64, an FP32 copy, descriptors
+    return wl.ndets * (8 * (2 * max_sub + 3) + 4) + 256 * 6 + 8 * 3 * 32 * 32
+
+
+def test_engine_holds_the_budget_when_the_table_estimate_is_too_low(B, alone):
+    # An admission estimate of one byte per string lets the second job be tried while the first one
+    # runs; its handle is then created under the budget that is really left, fails, and the job waits
+    # at the head of the queue until the first job has freed its memory.
+    jobs = _small_jobs()
+    real = {}
+    for i in (2, 3):
+        with B.SBD.from_workload(jobs[i]) as g:
+            real[i] = _basis(jobs[i]) + g.memory()
+    low2 = _basis(jobs[2]) + 16 * jobs[2].ndets + (jobs[2].A.size + jobs[2].B.size)
+    assert low2 < real[2]
+    budget = int(real[3] + low2 + 0.5 * (real[2] - low2))
+    assert budget < real[2] + real[3]
+    with _engine(B, hbm_budget_bytes=budget, table_bytes_per_string=1) as e:
+        j3 = e.submit(jobs[3], tol=TOL, tol_energy=TOL_E, keep_vector=True)
+        j2 = e.submit(jobs[2], tol=TOL, tol_energy=TOL_E, keep_vector=True)
+        e.run()
+        st = e.stats()
+        assert st["requeued"] >= 1 and st["done"] == 2
+        assert st["bytes_peak"] <= budget
+        r2, r3 = e.result(j2), e.result(j3)
+        assert r2["status"] == 0 and r3["status"] == 0
+        assert r3["t_done"] <= r2["t_admit"]
+        assert r2["energy"] == alone[2][0]["energy"] and r3["energy"] == alone[3][0]["energy"]
+        assert np.array_equal(e.vector(j2, r2["ndets"]), alone[2][1])
+
+
 def test_engine_reports_a_failing_job_and_finishes_the_others(B, alone):
     jobs = _small_jobs()
     bad = W.make("dup", 12, 4, 4, 220, 180, 0.25, 21)

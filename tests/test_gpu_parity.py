@@ -165,6 +165,11 @@ def test_sigma_fp64_unequal_electrons_and_sets(torch, B, oracle_mod):
         for prec in ("fp64", "f32x2"):
             got = g.sigma(torch.from_numpy(x[0]).cuda(), prec).cpu().numpy()
             assert rel_maxnorm(got, ref) <= SIGMA_FP64_RTOL, prec
+        assert rel_maxnorm(_mixed(torch, g, x[0]), ref) <= SIGMA_MIXED_RTOL
+
+
+def _mixed(torch, g, x):
+    return g.sigma(torch.from_numpy(np.asarray(x)).float().cuda(), "mixed").cpu().numpy()
 
 
 def test_sigma_mixed_against_fp64(torch, B, med_pair):
@@ -181,6 +186,25 @@ def test_sigma_is_deterministic(torch, B, med_pair):
     a = g.sigma(x, "fp64")
     b = g.sigma(x, "fp64")
     assert torch.equal(a, b)
+    # the mixed alpha-beta pass adds through shared-memory atomics, in fixed point: still bitwise
+    a = g.sigma(x.float(), "mixed")
+    b = g.sigma(x.float(), "mixed")
+    assert torch.equal(a, b)
+
+
+def test_sigma_mixed_several_alpha_chunks(torch, B, oracle_mod):
+    # the full norb=13, 5-electron alpha space: every string has 40 in-set singles, taken by the
+    # mixed alpha-beta pass as a 32-wide and an 8-wide chunk; a ragged beta set of 61 strings
+    A = W.all_strings(13, 5)
+    Bs = W.gumbel_top_k(13, 3, 61, 0.2, np.random.default_rng(9))
+    h, eri = W.one_electron(13, 9), W.two_electron(13, 9)
+    with B.SBD(13, 5, 3, h, eri, A, Bs) as g:
+        o = oracle_mod.Oracle(13, 5, 3, h, eri, A, Bs)
+        x = W.random_vector(g.N, 12)[0]
+        ref = o.sigma(x[None, :])[0]
+        assert rel_maxnorm(_mixed(torch, g, x), ref) <= SIGMA_MIXED_RTOL
+        assert rel_maxnorm(g.sigma(torch.from_numpy(x).cuda(), "fp64").cpu().numpy(), ref) <= SIGMA_FP64_RTOL
+        o.close()
 
 
 def test_sigma_hermitian_and_transpose_symmetric(torch, B):
@@ -222,6 +246,7 @@ def test_sigma_degenerate_single_string_sets(torch, B, oracle_mod, shape):
         for prec in ("fp64", "f32x2"):
             got = g.sigma(torch.from_numpy(x[0]).cuda(), prec).cpu().numpy()
             assert rel_maxnorm(got, o.sigma(x)[0]) <= SIGMA_FP64_RTOL, prec
+        assert rel_maxnorm(_mixed(torch, g, x[0]), o.sigma(x)[0]) <= SIGMA_MIXED_RTOL
 
 
 def test_sigma_zero_and_full_shells(torch, B, oracle_mod):
@@ -237,6 +262,7 @@ def test_sigma_zero_and_full_shells(torch, B, oracle_mod):
             for prec in ("fp64", "f32x2"):
                 got = g.sigma(torch.from_numpy(x[0]).cuda(), prec).cpu().numpy()
                 assert rel_maxnorm(got, o.sigma(x)[0]) <= SIGMA_FP64_RTOL, prec
+            assert rel_maxnorm(_mixed(torch, g, x[0]), o.sigma(x)[0]) <= SIGMA_MIXED_RTOL
 
 
 def test_h2_minimal_basis_golden(torch, B, oracle_mod):
@@ -252,6 +278,7 @@ def test_h2_minimal_basis_golden(torch, B, oracle_mod):
         for prec in ("fp64", "f32x2"):
             got = g.sigma(torch.from_numpy(x[0]).cuda(), prec).cpu().numpy()
             assert rel_maxnorm(got, o.sigma(x)[0]) <= SIGMA_FP64_RTOL, prec
+        assert rel_maxnorm(_mixed(torch, g, x[0]), o.sigma(x)[0]) <= SIGMA_MIXED_RTOL
         res = g.davidson(nroots=1, tol=1e-10, precision="fp64")
         assert res.status == 0
         assert abs(res.energies[0] - e_dense) <= 1e-12
@@ -284,6 +311,7 @@ def test_sigma_norb_64(torch, B, oracle_mod):
         for prec in ("fp64", "f32x2"):
             got = g.sigma(torch.from_numpy(x[0]).cuda(), prec).cpu().numpy()
             assert rel_maxnorm(got, o.sigma(x)[0]) <= SIGMA_FP64_RTOL, prec
+        assert rel_maxnorm(_mixed(torch, g, x[0]), o.sigma(x)[0]) <= SIGMA_MIXED_RTOL
 
 
 # ---------------------------------------------------------------------------

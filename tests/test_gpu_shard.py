@@ -87,7 +87,16 @@ def test_ring_driver_on_one_rank_and_plan_errors(torch, B):
         out = torch.empty(g.N, dtype=torch.float64, device="cuda")
         ring(x, out)
         close()
-        assert rel_maxnorm(out.cpu().numpy(), g.sigma(x, "fp64").cpu().numpy()) <= 1e-15
+        ref = g.sigma(x, "fp64").cpu().numpy()
+        assert rel_maxnorm(out.cpu().numpy(), ref) <= 1e-15
+        # products on a side stream: ordered after the ring's zeroing on the current stream, and the
+        # current stream waits for them (the output is read there right after)
+        side = torch.cuda.Stream()
+        fn, close = shard.device_block_sigma(g.handle, bounds, 0, "fp64", stream=side)
+        out.fill_(float("nan"))
+        shard.RingSigma(fn, bounds, 0, 1, g.nB)(x, out)
+        close()
+        assert rel_maxnorm(out.cpu().numpy(), ref) <= 1e-15
         for r0, r1, j0, j1 in [(5, 5, 0, 3), (0, g.nA + 1, 0, 3), (0, 3, -1, 2), (0, 3, 2, 1)]:
             with pytest.raises(B.SbdError):
                 B.sbd_block_plan_create(g.handle, r0, r1, j0, j1)

@@ -61,6 +61,10 @@ def test_oracle_equals_second_quantisation(oracle_mod, norb, na, nb, nA, nB, see
     ref = secondq.selected_block(Hf, norb, o.sorted_strings(0), o.sorted_strings(1))
     got = o.dense()
     assert np.abs(got - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max())
+    # the diagonal entry point (used for the preconditioner, Sec. II-E) on its own
+    d = o.diag()
+    assert np.abs(d - np.diag(ref)).max() <= 1e-13 * max(1.0, np.abs(ref).max())
+    assert np.array_equal(d, np.diag(got))
 
 
 def test_string_tables_signs_against_jordan_wigner(oracle_mod):
