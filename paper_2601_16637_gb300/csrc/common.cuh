@@ -81,8 +81,9 @@ struct SpinTables {
     float2 *d_vx2 = nullptr;   // d_v64_sig as FP32 pairs
     // Source-major singles for the column-stationary alpha-beta pass.  The canonical singles list
     // of each string is cut into items of at most kSrcItem entries (strings in ascending order,
-    // each string's items consecutive), so that the lanes of a warp, one item each, walk lists of
-    // nearly equal length; item t = string | entries << 18 (src_item[t]); entry i of item t is
+    // each string's items consecutive, then inside each slice of 32 items the full ones first and
+    // the partial ones by decreasing length), so that the lanes of a warp, one item each, walk
+    // lists of nearly equal length; item t = string | entries << 18 (src_item[t]); entry i of item t is
     // src_ent[(t / 32) * 32 * kSrcItem + 32 * i + t % 32] (coalesced for the 32 items of a warp):
     // target (bits 0-17) | index of the unordered orbital pair {p, q} (bits 18-28) | phase -1 (bit 29).
     uint32_t *src_item = nullptr;

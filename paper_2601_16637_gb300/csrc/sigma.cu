@@ -177,25 +177,34 @@ __device__ __forceinline__ int pk_code(uint32_t pk) { return (int)(pk >> (kPackK
 __device__ __forceinline__ bool pk_neg(uint32_t pk) { return ((pk >> kPackKeyShift) & 1u) != 0u; }
 
 // Excitation lists of the column spin (padded sigma copies), in the layout each precision
-// reads.  Every list starts at a multiple of kListPad entries, so a lane fetches 4 entries with
-// 16-byte loads.
+// reads.  Every list starts at a multiple of kListPad entries.  The 8 lanes of a group read a
+// list in chunks of up to 32 slots: in a chunk of Lc slots (32, or what is left at the end) lane l
+// takes slots {2l, 2l+1} and {Lc/2 + 2l, Lc/2 + 2l + 1}, so each of the group's two loads reads
+// one contiguous run of Lc/2 entries; entry u of the lane is slot (u/2)*(Lc/2) + 2l + u%2, the
+// slot the u-th 128-bit shared-memory phase of the pass gathers for that lane.
+__device__ __forceinline__ void list_slots(int64_t s0, int cb, int lc, int lig, int64_t &e0, int64_t &e1)
+{
+    e0 = s0 + cb + 2 * lig;
+    e1 = s0 + cb + lc / 2 + 2 * lig;
+}
+
 template <typename T>
 struct Lists;
 template <>
 struct Lists<float> {
     const uint2 *s;  // (packed single, value bits)
     const uint2 *d;  // (target, value bits)
-    __device__ void singles4(int64_t e, uint32_t (&pk)[4], float (&v)[4]) const
+    __device__ void singles4(int64_t e0, int64_t e1, uint32_t (&pk)[4], float (&v)[4]) const
     {
-        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(s + e));
-        const uint4 b = __ldg(reinterpret_cast<const uint4 *>(s + e + 2));
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(s + e0));
+        const uint4 b = __ldg(reinterpret_cast<const uint4 *>(s + e1));
         pk[0] = a.x, v[0] = __uint_as_float(a.y), pk[1] = a.z, v[1] = __uint_as_float(a.w);
         pk[2] = b.x, v[2] = __uint_as_float(b.y), pk[3] = b.z, v[3] = __uint_as_float(b.w);
     }
-    __device__ void doubles4(int64_t e, int (&j)[4], float (&v)[4]) const
+    __device__ void doubles4(int64_t e0, int64_t e1, int (&j)[4], float (&v)[4]) const
     {
-        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(d + e));
-        const uint4 b = __ldg(reinterpret_cast<const uint4 *>(d + e + 2));
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(d + e0));
+        const uint4 b = __ldg(reinterpret_cast<const uint4 *>(d + e1));
         j[0] = (int)a.x, v[0] = __uint_as_float(a.y), j[1] = (int)a.z, v[1] = __uint_as_float(a.w);
         j[2] = (int)b.x, v[2] = __uint_as_float(b.y), j[3] = (int)b.z, v[3] = __uint_as_float(b.w);
     }
@@ -206,20 +215,22 @@ struct Lists<double> {
     const double *sv;
     const int32_t *dj;
     const double *dv;
-    __device__ void singles4(int64_t e, uint32_t (&pk)[4], double (&v)[4]) const
+    __device__ void singles4(int64_t e0, int64_t e1, uint32_t (&pk)[4], double (&v)[4]) const
     {
-        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(spk + e));
-        const double2 b = __ldg(reinterpret_cast<const double2 *>(sv + e));
-        const double2 c = __ldg(reinterpret_cast<const double2 *>(sv + e + 2));
-        pk[0] = a.x, pk[1] = a.y, pk[2] = a.z, pk[3] = a.w;
+        const uint2 a = __ldg(reinterpret_cast<const uint2 *>(spk + e0));
+        const uint2 a1 = __ldg(reinterpret_cast<const uint2 *>(spk + e1));
+        const double2 b = __ldg(reinterpret_cast<const double2 *>(sv + e0));
+        const double2 c = __ldg(reinterpret_cast<const double2 *>(sv + e1));
+        pk[0] = a.x, pk[1] = a.y, pk[2] = a1.x, pk[3] = a1.y;
         v[0] = b.x, v[1] = b.y, v[2] = c.x, v[3] = c.y;
     }
-    __device__ void doubles4(int64_t e, int (&j)[4], double (&v)[4]) const
+    __device__ void doubles4(int64_t e0, int64_t e1, int (&j)[4], double (&v)[4]) const
     {
-        const int4 a = __ldg(reinterpret_cast<const int4 *>(dj + e));
-        const double2 b = __ldg(reinterpret_cast<const double2 *>(dv + e));
-        const double2 c = __ldg(reinterpret_cast<const double2 *>(dv + e + 2));
-        j[0] = a.x, j[1] = a.y, j[2] = a.z, j[3] = a.w;
+        const int2 a = __ldg(reinterpret_cast<const int2 *>(dj + e0));
+        const int2 a1 = __ldg(reinterpret_cast<const int2 *>(dj + e1));
+        const double2 b = __ldg(reinterpret_cast<const double2 *>(dv + e0));
+        const double2 c = __ldg(reinterpret_cast<const double2 *>(dv + e1));
+        j[0] = a.x, j[1] = a.y, j[2] = a1.x, j[3] = a1.y;
         v[0] = b.x, v[1] = b.y, v[2] = c.x, v[3] = c.y;
     }
 };
@@ -230,20 +241,22 @@ struct Lists<F2> {
     const float2 *sv;
     const int32_t *dj;
     const float2 *dv;
-    __device__ void singles4(int64_t e, uint32_t (&pk)[4], F2 (&v)[4]) const
+    __device__ void singles4(int64_t e0, int64_t e1, uint32_t (&pk)[4], F2 (&v)[4]) const
     {
-        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(spk + e));
-        const float4 b = __ldg(reinterpret_cast<const float4 *>(sv + e));
-        const float4 c = __ldg(reinterpret_cast<const float4 *>(sv + e + 2));
-        pk[0] = a.x, pk[1] = a.y, pk[2] = a.z, pk[3] = a.w;
+        const uint2 a = __ldg(reinterpret_cast<const uint2 *>(spk + e0));
+        const uint2 a1 = __ldg(reinterpret_cast<const uint2 *>(spk + e1));
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(sv + e0));
+        const float4 c = __ldg(reinterpret_cast<const float4 *>(sv + e1));
+        pk[0] = a.x, pk[1] = a.y, pk[2] = a1.x, pk[3] = a1.y;
         v[0] = F2(b.x, b.y), v[1] = F2(b.z, b.w), v[2] = F2(c.x, c.y), v[3] = F2(c.z, c.w);
     }
-    __device__ void doubles4(int64_t e, int (&j)[4], F2 (&v)[4]) const
+    __device__ void doubles4(int64_t e0, int64_t e1, int (&j)[4], F2 (&v)[4]) const
     {
-        const int4 a = __ldg(reinterpret_cast<const int4 *>(dj + e));
-        const float4 b = __ldg(reinterpret_cast<const float4 *>(dv + e));
-        const float4 c = __ldg(reinterpret_cast<const float4 *>(dv + e + 2));
-        j[0] = a.x, j[1] = a.y, j[2] = a.z, j[3] = a.w;
+        const int2 a = __ldg(reinterpret_cast<const int2 *>(dj + e0));
+        const int2 a1 = __ldg(reinterpret_cast<const int2 *>(dj + e1));
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(dv + e0));
+        const float4 c = __ldg(reinterpret_cast<const float4 *>(dv + e1));
+        j[0] = a.x, j[1] = a.y, j[2] = a1.x, j[3] = a1.y;
         v[0] = F2(b.x, b.y), v[1] = F2(b.z, b.w), v[2] = F2(c.x, c.y), v[3] = F2(c.z, c.w);
     }
 };
@@ -365,10 +378,14 @@ __device__ __forceinline__ void row_group(const RowArgs<T> &a, int64_t r0, unsig
             for (int r = 0; r < R; ++r) acc[r] = T(0);
             if (valid) {
                 const int ls = (int)(s1 - s0), ld = (int)(d1 - d0);
-                for (int i = kListPad * lig; i < ls; i += kGroup * kListPad) {
+                for (int cb = 0; cb < ls; cb += kGroup * kListPad) {
+                    const int lc = min(kGroup * kListPad, ls - cb);
+                    if (kListPad * lig >= lc) break;
+                    int64_t e0, e1;
+                    list_slots(s0, cb, lc, lig, e0, e1);
                     uint32_t pk[4];
                     T v[4];
-                    a.lists.singles4(s0 + i, pk, v);
+                    a.lists.singles4(e0, e1, pk, v);
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         T xj[R], jv[R];
@@ -386,10 +403,32 @@ __device__ __forceinline__ void row_group(const RowArgs<T> &a, int64_t r0, unsig
                         }
                     }
                 }
-                for (int i = kListPad * lig; i < ld; i += kGroup * kListPad) {
+                // doubles: the next chunk's entries are loaded before the current chunk is used,
+                // so the L2 latency of the list overlaps the gathers
+                constexpr int kChunk = kGroup * kListPad;
+                int jn[4];
+                T vn[4];
+                bool more = 0 < ld && kListPad * lig < min(kChunk, ld);
+                if (more) {
+                    int64_t e0, e1;
+                    list_slots(d0, 0, min(kChunk, ld), lig, e0, e1);
+                    a.lists.doubles4(e0, e1, jn, vn);
+                }
+                for (int cb = 0; more; cb += kChunk) {
                     int jj[4];
                     T v[4];
-                    a.lists.doubles4(d0 + i, jj, v);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        jj[u] = jn[u];
+                        v[u] = vn[u];
+                    }
+                    const int cn = cb + kChunk;
+                    more = cn < ld && kListPad * lig < min(kChunk, ld - cn);
+                    if (more) {
+                        int64_t e0, e1;
+                        list_slots(d0, cn, min(kChunk, ld - cn), lig, e0, e1);
+                        a.lists.doubles4(e0, e1, jn, vn);
+                    }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         T xj[R];
@@ -530,9 +569,14 @@ __device__ __forceinline__ void ab_row(const AbArgs<T> &a, int64_t ia, unsigned 
                 T acc = T(0);
                 if (valid) {
                     const int lb = (int)(b1 - b0);
-                    for (int i = kListPad * lig; i < lb; i += kGroup * kListPad) {
-                        const uint4 p4 = __ldg(reinterpret_cast<const uint4 *>(a.bs_pk + b0 + i));
-                        const uint32_t pk[4] = {p4.x, p4.y, p4.z, p4.w};
+                    for (int cb = 0; cb < lb; cb += kGroup * kListPad) {
+                        const int lc = min(kGroup * kListPad, lb - cb);
+                        if (kListPad * lig >= lc) break;
+                        int64_t e0, e1;
+                        list_slots(b0, cb, lc, lig, e0, e1);
+                        const uint2 pa = __ldg(reinterpret_cast<const uint2 *>(a.bs_pk + e0));
+                        const uint2 pb = __ldg(reinterpret_cast<const uint2 *>(a.bs_pk + e1));
+                        const uint32_t pk[4] = {pa.x, pa.y, pb.x, pb.y};
                         T part[4];
 #pragma unroll
                         for (int t = 0; t < 4; ++t) {
@@ -602,13 +646,19 @@ __global__ void __launch_bounds__(Threads<T>::value) ab_pass_kernel(const AbArgs
 // whatever rows they read; with KC = 16 (8) each row holds 2 (4) copies and lanes read their own
 // copy, rotated within it.  The lane's registers hold the amplitudes in the same rotated order.
 //
-// Determinism: the row accumulator holds 64-bit fixed-point integers with one scale per output row,
-// 2^e with e chosen so that the largest possible row sum,
-//   maxdeg_beta * max|(pq|rs)| * sum_k max_jb |C(ja_k, jb)|,
-// stays below 2^60; each FP32 dot product is rounded once onto that grid and integer addition is
-// exact and order independent, so the result does not depend on the order of the shared-memory
-// atomics.  The grid step is at most 2^-59 of that bound, far below FP32 rounding of the products.
-// The accumulated row is added to s(ia, :) in FP64 by the CTA that owns the row.
+// Determinism: each FP32 dot product is rounded once onto a fixed-point grid with one scale 2^e per
+// output row and added as an integer, and integer addition is exact and order independent, so the
+// result does not depend on the order of the shared-memory atomics.  An element of the row receives
+// at most m = maxdeg_beta * (chunks of the row) contributions v.  Each v is split as
+// v = hi * 2^L + lo with 0 <= lo < 2^L, L = 32 - bitlength(m), and lo and hi are added with 32-bit
+// integer atomics into two words per element (random 32-bit shared-memory atomics run several times
+// faster than 64-bit ones): the lo word cannot overflow (m * 2^L < 2^32), and e is chosen so that
+// the largest possible row sum of |v|,
+//   maxdeg_beta * max|(pq|rs)| * sum_k max_jb |C(ja_k, jb)|  (times 2^e),
+// stays below 2^(30+L), which keeps the sum of the hi words inside a signed 32-bit word.  The grid
+// step is then about 2^-(30+L) >= 2^-52 of that bound, far below FP32 rounding of the products.
+// The element is hi_sum * 2^L + lo_sum exactly; the row is added to s(ia, :) in FP64 by the CTA
+// that owns the row.
 
 constexpr int kSrcThreads = 1024;
 
@@ -625,6 +675,7 @@ struct AbSrcArgs {
     int64_t src_nitem;
     const float *rowmax;      // [nA] max |C(ja, :)|
     float bound;              // maxdeg_beta * max |(pq|rs)|
+    int maxdeg;               // maxdeg_beta: most singles of a beta string
 };
 
 // shared memory of one CTA: W [npair][8] float4, accumulator [nB] u64, pair -> rs code
@@ -634,9 +685,20 @@ __host__ __device__ inline size_t src_smem(int npair, int64_t nB)
     return src_w_bytes(npair) + (size_t)nB * 8 + round16((size_t)npair * 2);
 }
 
+// adds t * f to element ib of the row accumulator (words lo[ib], hi[ib]; see above)
+__device__ __forceinline__ void src_add(unsigned *acc_lo, unsigned *acc_hi, uint32_t e, float f, float scale,
+                                        int lbits)
+{
+    long long v = __float2ll_rn(f * scale);
+    if ((e >> kSrcNegBit) & 1u) v = -v;
+    const int ib = (int)(e & kPackJMask);
+    atomicAdd(acc_lo + ib, (unsigned)v & ((1u << lbits) - 1u));
+    atomicAdd(acc_hi + ib, (unsigned)(int)(v >> lbits));
+}
+
 template <int KC>
-__device__ __forceinline__ void src_chunk(const AbSrcArgs &a, const float4 *__restrict__ Wt,
-                                          unsigned long long *acc, const int *ja_s, int kc, float scale,
+__device__ __forceinline__ void src_chunk(const AbSrcArgs &a, const float4 *__restrict__ Wt, unsigned *acc_lo,
+                                          unsigned *acc_hi, const int *ja_s, int kc, float scale, int lbits,
                                           int *ctr)
 {
     constexpr int CPW = KC / 4;  // 16-byte chunks per copy of a W row
@@ -703,14 +765,8 @@ __device__ __forceinline__ void src_chunk(const AbSrcArgs &a, const float4 *__re
                     f0 = fmaf(x0.w, cv[4 * s + 3], f0);
                     f1 = fmaf(x1.w, cv[4 * s + 3], f1);
                 }
-                long long v0 = __float2ll_rn(f0 * scale);
-                if ((e[i] >> kSrcNegBit) & 1u) v0 = -v0;
-                atomicAdd(acc + (e[i] & kPackJMask), (unsigned long long)v0);
-                if (two) {
-                    long long v1 = __float2ll_rn(f1 * scale);
-                    if ((e[i + 1] >> kSrcNegBit) & 1u) v1 = -v1;
-                    atomicAdd(acc + (e[i + 1] & kPackJMask), (unsigned long long)v1);
-                }
+                src_add(acc_lo, acc_hi, e[i], f0, scale, lbits);
+                if (two) src_add(acc_lo, acc_hi, e[i + 1], f1, scale, lbits);
             }
         }
     }
@@ -740,7 +796,8 @@ __device__ __forceinline__ void src_build_w(const AbSrcArgs &a, float4 *Wt, cons
 __device__ __forceinline__ void src_row(const AbSrcArgs &a, int64_t ia, unsigned char *smem)
 {
     float4 *Wt = reinterpret_cast<float4 *>(smem);
-    unsigned long long *acc = reinterpret_cast<unsigned long long *>(smem + src_w_bytes(a.npair));
+    unsigned *acc_lo = reinterpret_cast<unsigned *>(smem + src_w_bytes(a.npair));
+    unsigned *acc_hi = acc_lo + a.nB;
     const int16_t *rs_of = reinterpret_cast<const int16_t *>(smem + src_w_bytes(a.npair) + (size_t)a.nB * 8);
     __shared__ __align__(16) int ja_s[32];
     __shared__ int pq_s[32];
@@ -748,12 +805,13 @@ __device__ __forceinline__ void src_row(const AbSrcArgs &a, int64_t ia, unsigned
     __shared__ int ctr;
     __shared__ float s_scale;
     __shared__ double s_inv;
+    __shared__ int s_lbits;
     __shared__ int s_state;  // 0 skip the row, 1 accumulate, 2 non-finite amplitudes
     const int tid = threadIdx.x;
     const int64_t e0 = a.as_ptr[ia];
     const int K = (int)(a.as_ptr[ia + 1] - e0);
     __syncthreads();  // the previous row is finished with shared memory
-    for (int64_t ib = tid; ib < a.nB; ib += blockDim.x) acc[ib] = 0ull;
+    for (int64_t ib = tid; ib < a.nB; ib += blockDim.x) acc_lo[ib] = acc_hi[ib] = 0u;
     {
         int16_t *rs_w = reinterpret_cast<int16_t *>(smem + src_w_bytes(a.npair) + (size_t)a.nB * 8);
         for (int r = 1; r < a.norb; ++r)
@@ -771,10 +829,14 @@ __device__ __forceinline__ void src_row(const AbSrcArgs &a, int64_t ia, unsigned
             } else if (bnd == 0.0) {
                 s_state = 0;
             } else {
-                int e = 60 - ilogb(bnd) - 1;  // bnd < 2^(ilogb+1), so bnd * 2^e < 2^60
+                // contributions per element: at most maxdeg per chunk of the row
+                const long long m = (long long)max(a.maxdeg, 1) * ((K + 31) / 32);
+                const int lbits = max(1, 32 - (64 - __clzll(m)));
+                int e = 30 + lbits - ilogb(bnd) - 1;  // bnd < 2^(ilogb+1), so bnd * 2^e < 2^(30+lbits)
                 e = max(-120, min(120, e));
                 s_scale = ldexpf(1.f, e);
                 s_inv = ldexp(1.0, -e);
+                s_lbits = lbits;
                 s_state = 1;
             }
         }
@@ -787,6 +849,7 @@ __device__ __forceinline__ void src_row(const AbSrcArgs &a, int64_t ia, unsigned
         return;
     }
     const float scale = s_scale;
+    const int lbits = s_lbits;
     for (int k0 = 0; k0 < K; k0 += 32) {
         const int kc = min(32, K - k0);
         __syncthreads();  // the previous chunk is finished with W and the chunk arrays
@@ -801,20 +864,23 @@ __device__ __forceinline__ void src_row(const AbSrcArgs &a, int64_t ia, unsigned
         if (kc <= 8) {
             src_build_w<8>(a, Wt, rs_of, pq_s, u_s, kc);
             __syncthreads();
-            src_chunk<8>(a, Wt, acc, ja_s, kc, scale, &ctr);
+            src_chunk<8>(a, Wt, acc_lo, acc_hi, ja_s, kc, scale, lbits, &ctr);
         } else if (kc <= 16) {
             src_build_w<16>(a, Wt, rs_of, pq_s, u_s, kc);
             __syncthreads();
-            src_chunk<16>(a, Wt, acc, ja_s, kc, scale, &ctr);
+            src_chunk<16>(a, Wt, acc_lo, acc_hi, ja_s, kc, scale, lbits, &ctr);
         } else {
             src_build_w<32>(a, Wt, rs_of, pq_s, u_s, kc);
             __syncthreads();
-            src_chunk<32>(a, Wt, acc, ja_s, kc, scale, &ctr);
+            src_chunk<32>(a, Wt, acc_lo, acc_hi, ja_s, kc, scale, lbits, &ctr);
         }
     }
     __syncthreads();
     const double inv = s_inv;
-    for (int64_t ib = tid; ib < a.nB; ib += blockDim.x) a.S[ia * a.nB + ib] += (double)(long long)acc[ib] * inv;
+    for (int64_t ib = tid; ib < a.nB; ib += blockDim.x) {
+        const long long v = (long long)(int)acc_hi[ib] * (1ll << lbits) + (long long)acc_lo[ib];
+        a.S[ia * a.nB + ib] += (double)v * inv;
+    }
 }
 
 __global__ void __launch_bounds__(kSrcThreads, 1) ab_src_kernel(const AbSrcArgs a)
@@ -914,6 +980,7 @@ AbSrcArgs src_args(const Ctx &c, const float *C, double *S, const float *rowmax)
     a.src_nitem = tb.src_nitem;
     a.rowmax = rowmax;
     a.bound = (float)((double)tb.src_maxdeg * (double)c.eri_absmax);
+    a.maxdeg = tb.src_maxdeg;
     return a;
 }
 

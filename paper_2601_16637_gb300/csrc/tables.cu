@@ -352,19 +352,21 @@ __global__ void ediag_kernel(const uint64_t *S, int64_t n, int norb, const doubl
 }
 
 // Sigma order of each source's list.  The list is padded with empty slots to a multiple of
-// kListPad and laid out for 16-byte loads: lane l of an 8-lane group fetches slots 4l..4l+3 of
-// each 32-slot chunk, and one 128-bit shared-memory phase gathers slot 4l+u of every lane.
-// Entries are first ranked as rounds "rank 0 of every target residue mod 8, rank 1 of every
-// residue, ...", so that consecutive entries in that order have distinct residues where the
+// kListPad and read in chunks of up to 32 slots by an 8-lane group: in a chunk of Lc slots lane l
+// fetches slots {2l, 2l+1} and {Lc/2 + 2l, Lc/2 + 2l + 1} (each of the group's two loads reads a
+// contiguous run), and the u-th 128-bit shared-memory phase gathers slot (u/2)*(Lc/2) + 2l + u%2 of
+// every lane l.  Entries are first ranked as rounds "rank 0 of every target residue mod 8, rank 1 of
+// every residue, ...", so that consecutive entries in that order have distinct residues where the
 // residue counts allow; each phase then receives a run of consecutive positions.
-// round-order position q of a list of Lp slots -> slot: in a chunk of Lc slots (32, or what is left of
-// a short list) m = Lc/4 lanes each fetch 4 slots, and phase u gathers slot 4*l + u of every lane l;
-// position m*u + l goes to slot 4*l + u, so each phase reads m consecutive round-order positions
+// round-order position q of a list of Lp slots -> slot: with m = Lc/4 lanes in the chunk, position
+// m*u + l goes to the slot phase u gathers for lane l, so each phase reads m consecutive positions
 __device__ __forceinline__ int slot_of(int q, int Lp)
 {
     const int chunk = q / 32, within = q % 32;
-    const int m = min(32, Lp - chunk * 32) / 4;
-    return chunk * 32 + 4 * (within % m) + within / m;
+    const int lc = min(32, Lp - chunk * 32);
+    const int m = lc / 4;
+    const int u = within / m, l = within % m;
+    return chunk * 32 + (u / 2) * (lc / 2) + 2 * l + (u % 2);
 }
 
 // Singles lists, where the gathers read two tables: staged amplitudes by target j and coefficient
@@ -491,6 +493,30 @@ __global__ void src_fill_kernel(const int64_t *__restrict__ ptr, const uint32_t 
             ent[(t / 32) * 32 * kSrcItem + 32 * slot + (t % 32)] =
                 (v & kPackJMask) | (pair << kSrcPairShift) | (neg << kSrcNegBit);
         }
+    }
+}
+
+// Order of the items inside each slice of 32: full items first, then the partial ones by decreasing
+// length (stable), so that in every round of the alpha-beta pass the lanes that still have a single
+// form a prefix of the warp and whole quarter-warps go idle together.  One warp per slice.
+__global__ void src_slice_order_kernel(const uint32_t *__restrict__ item_in, const uint32_t *__restrict__ ent_in,
+                                       int64_t nsl, uint32_t *item_out, uint32_t *ent_out)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; s < nsl;
+         s += (int64_t)gridDim.x * blockDim.x / 32) {
+        const uint32_t it = item_in[s * 32 + lane];
+        const int key = (int)(it >> kSrcPairShift);  // entries of the item, 0 for an empty slot
+        int rank = 0;
+        for (int c = kSrcItem; c >= 0; --c) {
+            const unsigned m = __ballot_sync(0xffffffffu, key == c);
+            if (c > key) rank += __popc(m);
+            else if (c == key) rank += __popc(m & lt);
+        }
+        item_out[s * 32 + rank] = it;
+        const int64_t base = s * 32 * kSrcItem;
+        for (int i = 0; i < kSrcItem; ++i) ent_out[base + 32 * i + rank] = ent_in[base + 32 * i + lane];
     }
 }
 
@@ -704,6 +730,15 @@ void build_tables(Ctx &c, int spin)
                                                                   t.src_ent);
         SBD_LAUNCH("src_fill_kernel");
         dfree(c, ioff);
+        uint32_t *item2 = dalloc_n<uint32_t>(c, (size_t)nsl * 32);
+        uint32_t *ent2 = dalloc_n<uint32_t>(c, (size_t)nsl * 32 * kSrcItem);
+        src_slice_order_kernel<<<blocks_for(nsl * 32, 256), 256, 0, c.stream>>>(t.src_item, t.src_ent, nsl, item2,
+                                                                                ent2);
+        SBD_LAUNCH("src_slice_order_kernel");
+        dfree(c, t.src_item);
+        dfree(c, t.src_ent);
+        t.src_item = item2;
+        t.src_ent = ent2;
     }
     t.ediag = dalloc_n<double>(c, n);
     ediag_kernel<<<blocks_for(n, 128), 128, 0, c.stream>>>(t.strings, n, norb, c.h64, c.eri64, t.ediag);
