@@ -276,11 +276,13 @@ int sbd_sort_strings_noalloc(const uint64_t *keys_dev, int64_t n, int norb, int 
  *   c_dev[i]     device pointer, handle i's [nA][nB] vector (float for
  *                SBD_MIXED, double for SBD_FP64), sorted-string order
  *   sigma_dev[i] device pointer, [nA][nB] doubles, written
- *   rows_per_item rows of C staged per work item: 1, 2 or (mixed) 4; 0 picks
- *                the largest that fits shared memory for every instance
+ *   rows_per_item rows of C staged per work item: 1, 2, or for SBD_MIXED 4 or 8
+ *                (8: one column half at a time); 0 picks the largest that fits
+ *                shared memory for every instance
  * Each output element is computed by the same arithmetic as sbd_sigma with
- * the same rows per item.  Enqueued on `stream` (the handles' work buffers are
- * used), then synchronised.
+ * the same rows per item (sbd_sigma takes 8 rows over column halves for
+ * SBD_MIXED where they fit, else the largest that fits).  Enqueued on `stream`
+ * (the handles' work buffers are used), then synchronised.
  */
 int sbd_sigma_batched(int n, const sbd_handle *handles, const void *const *c_dev, double *const *sigma_dev,
                       sbd_precision prec, int rows_per_item, void *stream);
@@ -367,7 +369,8 @@ typedef struct {
     int max_iter;            /* iterations per job (default 200) */
     int max_norb;            /* largest norb of a job (default 64) */
     int max_strings;         /* largest |A| or |B| of a job (default 20000) */
-    int rows_per_item;       /* mixed sigma rows per work item: 1, 2, 4; 0 = autotune at the first step */
+    int rows_per_item;       /* mixed sigma rows per work item: 1, 2, 4, 8 (over column halves); 0 = autotune at
+                                the first step */
     double delta;            /* preconditioner floor (default 1e-4) */
     size_t hbm_budget_bytes; /* admission budget for the jobs' device memory; 0 = unlimited */
     sbd_alloc_fn alloc;      /* NULL: cudaMallocAsync / cudaFreeAsync */
@@ -401,7 +404,7 @@ typedef struct {
     int64_t graph_launches;   /* CUDA graph replays */
     int64_t kernel_launches;  /* kernels run by this engine (graph nodes included) */
     int rows_per_item;        /* mixed sigma rows per work item in use */
-    double tune_ms[3];        /* autotuner: batched mixed sigma time with 4, 2, 1 rows (0 = not tried) */
+    double tune_ms[4];        /* autotuner: batched mixed sigma time with 8, 4, 2, 1 rows (0 = not tried) */
     size_t bytes_in_use;      /* device bytes held for admitted jobs */
     size_t bytes_peak;
     int active, pending, done;

@@ -74,7 +74,7 @@ class sbd_job_result(C.Structure):
 
 class sbd_engine_stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("graph_launches", C.c_int64), ("kernel_launches", C.c_int64),
-                ("rows_per_item", C.c_int), ("tune_ms", C.c_double * 3), ("bytes_in_use", C.c_size_t),
+                ("rows_per_item", C.c_int), ("tune_ms", C.c_double * 4), ("bytes_in_use", C.c_size_t),
                 ("bytes_peak", C.c_size_t), ("active", C.c_int), ("pending", C.c_int), ("done", C.c_int),
                 ("requeued", C.c_int64)]
 

@@ -197,9 +197,8 @@ int sbd_sigma_batched(int n, const sbd_handle *handles, const void *const *c_dev
         }
         int R = rows_per_item;
         if (R == 0) {
-            for (int cand : {4, 2, 1}) {
-                if (cand == 4 && prec != SBD_MIXED) continue;
-                if (sigma_batch_smem(prec, cand, max_strings, max_norb) <= sigma_batch_smem_limit(device)) {
+            for (int cand : {8, 4, 2, 1}) {
+                if (sigma_batch_fits(prec, cand, max_strings, max_norb, device)) {
                     R = cand;
                     break;
                 }

@@ -79,6 +79,14 @@ struct SpinTables {
     uint2 *d_jv32 = nullptr;   // (d_j_sig, FP32 value bits), for the mixed sigma
     float2 *s_vx2 = nullptr;   // s_v64_sig as FP32 pairs (hi, lo), for the FP32-pair sigma
     float2 *d_vx2 = nullptr;   // d_v64_sig as FP32 pairs
+    // Mixed-sigma lists split at the middle of the string set (half = (n + 1) / 2): virtual list
+    // 2i holds the entries of source i with target < half, list 2i + 1 those with target >= half,
+    // each padded to kListPad and in sigma order, for row passes that stage one column half at a
+    // time (8 rows instead of 4 in the same shared memory).
+    int64_t half = 0;
+    int64_t *hs_ptr = nullptr, *hd_ptr = nullptr;  // [2n + 1]
+    uint2 *hs = nullptr;  // (packed single, FP32 value bits)
+    uint2 *hd = nullptr;  // (target, FP32 value bits)
     // Source-major singles for the column-stationary alpha-beta pass.  The canonical singles list
     // of each string is cut into items of at most kSrcItem entries (strings in ascending order,
     // each string's items consecutive, then inside each slice of 32 items the full ones first and
@@ -242,11 +250,15 @@ struct SigmaSlot {
 };
 struct SigmaBatch;
 // Device descriptors for up to max_slots instances whose string sets have at most max_strings
-// entries per spin and norb <= max_norb; R = rows staged per work item (1, 2 or 4 (FP32 only)).
+// entries per spin and norb <= max_norb; R = rows staged per work item (1, 2, or for the mixed
+// precision 4, or 8 over column halves).
 SigmaBatch *sigma_batch_create(int max_slots, sbd_precision prec, int R, int max_strings, int max_norb, int device);
 // Shared memory one work item needs with R staged rows; compare with sigma_batch_smem_limit().
 size_t sigma_batch_smem(sbd_precision prec, int R, int max_strings, int max_norb);
 size_t sigma_batch_smem_limit(int device);
+// whether R rows per item (8: mixed only, over column halves, with the column-stationary alpha-beta
+// pass) fits shared memory for max_strings and max_norb
+bool sigma_batch_fits(sbd_precision prec, int R, int max_strings, int max_norb, int device);
 // Fills the host staging copy of the descriptors (no device work).
 void sigma_batch_set(SigmaBatch *b, const SigmaSlot *slots, int n);
 // Copies the staged descriptors to the device and runs transpose, beta, alpha and alpha-beta

@@ -581,7 +581,7 @@ struct sbd_engine_s {
     int64_t *small_idx = nullptr;
     SigmaBatch *sb32 = nullptr, *sb64 = nullptr;
     int rows_per_item = 0;
-    double tune_ms[3] = {0, 0, 0};
+    double tune_ms[4] = {0, 0, 0, 0};
     cudaGraphExec_t gA = nullptr, gB = nullptr;
     int64_t launches_A = 0, launches_B = 0;
     int64_t steps = 0, graph_launches = 0, kernel_launches = 0;
@@ -1045,12 +1045,12 @@ void sbd_engine_s::autotune()
     cudaEvent_t a, b;
     SBD_CUDA(cudaEventCreate(&a));
     SBD_CUDA(cudaEventCreate(&b));
-    const int cand[3] = {4, 2, 1};
+    const int cand[4] = {8, 4, 2, 1};
     float best = INFINITY;
     int best_r = 0;
-    for (int ci = 0; ci < 3; ++ci) {
+    for (int ci = 0; ci < 4; ++ci) {
         const int R = cand[ci];
-        if (sigma_batch_smem(SBD_MIXED, R, ms, opt.max_norb) > sigma_batch_smem_limit(device)) continue;
+        if (!sigma_batch_fits(SBD_MIXED, R, ms, opt.max_norb, device)) continue;
         SigmaBatch *sb = sigma_batch_create(opt.max_slots, SBD_MIXED, R, ms, opt.max_norb, device);
         float t = INFINITY;
         for (int rep = 0; rep < 3; ++rep) {
@@ -1236,7 +1236,8 @@ int sbd_engine_create(sbd_engine *out, const sbd_engine_options *opt, void *stre
     if (o.max_slots < 1 || o.max_slots > 1024 || o.max_subspace < 3 || o.max_subspace > kEMaxSub ||
         o.max_iter < 1 || o.max_norb < 1 || o.max_norb > 64 || o.max_strings < 1 ||
         o.max_strings > (int)kMaxStringsPerSpin || !(o.rows_per_item == 0 || o.rows_per_item == 1 ||
-                                                     o.rows_per_item == 2 || o.rows_per_item == 4) ||
+                                                     o.rows_per_item == 2 || o.rows_per_item == 4 ||
+                                                     o.rows_per_item == 8) ||
         !(o.delta > 0.0)) {
         set_thread_error("invalid engine options");
         return SBD_ERR_INVALID_ARG;
@@ -1385,7 +1386,7 @@ int sbd_engine_get_stats(sbd_engine e, sbd_engine_stats *out)
     out->graph_launches = e->graph_launches;
     out->kernel_launches = e->kernel_launches;
     out->rows_per_item = e->rows_per_item;
-    for (int i = 0; i < 3; ++i) out->tune_ms[i] = e->tune_ms[i];
+    for (int i = 0; i < 4; ++i) out->tune_ms[i] = e->tune_ms[i];
     out->bytes_in_use = e->bytes_in_use;
     out->bytes_peak = e->bytes_peak;
     out->requeued = e->requeued;

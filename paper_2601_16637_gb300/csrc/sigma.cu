@@ -178,14 +178,16 @@ __device__ __forceinline__ bool pk_neg(uint32_t pk) { return ((pk >> kPackKeyShi
 
 // Excitation lists of the column spin (padded sigma copies), in the layout each precision
 // reads.  Every list starts at a multiple of kListPad entries.  The 8 lanes of a group read a
-// list in chunks of up to 32 slots: in a chunk of Lc slots (32, or what is left at the end) lane l
-// takes slots {2l, 2l+1} and {Lc/2 + 2l, Lc/2 + 2l + 1}, so each of the group's two loads reads
-// one contiguous run of Lc/2 entries; entry u of the lane is slot (u/2)*(Lc/2) + 2l + u%2, the
-// slot the u-th 128-bit shared-memory phase of the pass gathers for that lane.
+// list in chunks of up to 32 slots: in a chunk, lane l takes slots 4l..4l+3 (two 2-entry loads),
+// and entry u of the lane is the slot the u-th 128-bit shared-memory phase of the pass gathers
+// for that lane.  (Taking the two halves of a chunk as two contiguous runs instead halves the
+// sectors each load touches but loses the L1 hits of the second load, and was slower at 1.0e8
+// determinants.)
 __device__ __forceinline__ void list_slots(int64_t s0, int cb, int lc, int lig, int64_t &e0, int64_t &e1)
 {
-    e0 = s0 + cb + 2 * lig;
-    e1 = s0 + cb + lc / 2 + 2 * lig;
+    (void)lc;
+    e0 = s0 + cb + 4 * lig;
+    e1 = e0 + 2;
 }
 
 template <typename T>
@@ -277,6 +279,10 @@ struct RowArgs {
     const double *eri;  // FP64 integrals, for the J vectors of the staged rows
     const int64_t *s_ptr, *d_ptr;
     Lists<T> lists;
+    // mixed passes over column halves (row_halves): the column spin's lists split at `half`
+    const int64_t *hls_ptr, *hld_ptr;  // singles, doubles: [2n + 1]
+    const uint2 *hls, *hld;
+    int64_t half;
 };
 
 // Gather pass over rows of X: each CTA stages R consecutive rows, then every
@@ -403,32 +409,14 @@ __device__ __forceinline__ void row_group(const RowArgs<T> &a, int64_t r0, unsig
                         }
                     }
                 }
-                // doubles: the next chunk's entries are loaded before the current chunk is used,
-                // so the L2 latency of the list overlaps the gathers
-                constexpr int kChunk = kGroup * kListPad;
-                int jn[4];
-                T vn[4];
-                bool more = 0 < ld && kListPad * lig < min(kChunk, ld);
-                if (more) {
+                for (int cb = 0; cb < ld; cb += kGroup * kListPad) {
+                    const int lc = min(kGroup * kListPad, ld - cb);
+                    if (kListPad * lig >= lc) break;
                     int64_t e0, e1;
-                    list_slots(d0, 0, min(kChunk, ld), lig, e0, e1);
-                    a.lists.doubles4(e0, e1, jn, vn);
-                }
-                for (int cb = 0; more; cb += kChunk) {
+                    list_slots(d0, cb, lc, lig, e0, e1);
                     int jj[4];
                     T v[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        jj[u] = jn[u];
-                        v[u] = vn[u];
-                    }
-                    const int cn = cb + kChunk;
-                    more = cn < ld && kListPad * lig < min(kChunk, ld - cn);
-                    if (more) {
-                        int64_t e0, e1;
-                        list_slots(d0, cn, min(kChunk, ld - cn), lig, e0, e1);
-                        a.lists.doubles4(e0, e1, jn, vn);
-                    }
+                    a.lists.doubles4(e0, e1, jj, v);
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         T xj[R];
@@ -477,6 +465,170 @@ __global__ void __launch_bounds__(Threads<T>::value) row_pass_kernel(const RowAr
 {
     extern __shared__ __align__(16) unsigned char smem[];
     for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < a.nrow; r0 += (int64_t)gridDim.x * R) row_group<T, R, STAGED>(a, r0, smem);
+}
+
+// Mixed-precision gather pass over 8 rows, one column half at a time.  With 4 rows the whole row
+// range fits shared memory; staging 8 rows of one half ([0, half) or [half, ncol)) in the same space
+// lets every excitation-list entry, loaded once from L2, feed 8 multiply-adds instead of 4.  Each
+// output column sums its entries with targets in the staged half (the split lists of the column
+// spin), writes that half's sum (with the diagonal term), and adds the other half's sum after the
+// second staging.  The 8 rows are kept as two 4-row interleaved arrays, so a 16-byte gather per
+// array has the bank pattern of the 4-row pass; the coefficient table of the singles likewise.
+constexpr int kHalfRows = 8;
+
+__host__ __device__ inline size_t halves_smem(int64_t half, int norb)
+{
+    return (size_t)32 * half + (size_t)64 * norb * norb;
+}
+
+__device__ __forceinline__ void row_halves(const RowArgs<float> &a, int64_t r0, unsigned char *smem)
+{
+    constexpr int kThreads = Threads<float>::value;
+    const int n2 = a.norb * a.norb;
+    const int64_t hw = a.half;  // rows of the staged arrays: the lower half is the wider one
+    float *Xa = reinterpret_cast<float *>(smem);                   // [hw][4]  rows 0-3
+    float *Xb = Xa + 4 * hw;                                        // [hw][4]  rows 4-7
+    float *Ja = Xb + 4 * hw;                                        // [2 n2][4]
+    float *Jb = Ja + 8 * n2;                                        // [2 n2][4]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gi = lane / kGroup, lig = lane % kGroup;
+    const int64_t ngroups = (kThreads / 32) * kGroupsPerWarp;
+    const int nr = (int)min((int64_t)kHalfRows, a.nrow - r0);
+    unsigned rmax[kHalfRows];
+#pragma unroll
+    for (int r = 0; r < kHalfRows; ++r) rmax[r] = 0u;
+    __shared__ unsigned red_h[kHalfRows];
+    __syncthreads();  // the previous row group is finished with shared memory
+    if (tid < kHalfRows) red_h[tid] = 0u;
+    // sign-folded J table of the 8 rows (row key = 2*code + neg; code 0 rows zero)
+    for (int key = tid; key < 2 * n2; key += kThreads) {
+        const int code = key >> 1;
+        float v[kHalfRows];
+#pragma unroll
+        for (int r = 0; r < kHalfRows; ++r) {
+            double sj = 0.0;
+            if (r < nr && code != 0)
+                for (uint64_t m = a.row_strings[r0 + r]; m; m &= m - 1ull) {
+                    const int k = __ffsll((long long)m) - 1;
+                    sj += __ldg(a.eri + (size_t)code * n2 + (size_t)k * (a.norb + 1));
+                }
+            v[r] = (float)((key & 1) ? -sj : sj);
+        }
+        *reinterpret_cast<float4 *>(Ja + (size_t)key * 4) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4 *>(Jb + (size_t)key * 4) = make_float4(v[4], v[5], v[6], v[7]);
+    }
+    for (int h = 0; h < 2; ++h) {
+        const int64_t c0 = h ? a.half : 0, c1 = h ? a.ncol : a.half;
+        if (h) __syncthreads();  // every column is finished with the first half
+        for (int64_t c = c0 + tid; c < c1; c += kThreads) {
+            float v[kHalfRows];
+#pragma unroll
+            for (int r = 0; r < kHalfRows; ++r) v[r] = r < nr ? a.X[(r0 + r) * a.ncol + c] : 0.f;
+            *reinterpret_cast<float4 *>(Xa + (c - c0) * 4) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4 *>(Xb + (c - c0) * 4) = make_float4(v[4], v[5], v[6], v[7]);
+#pragma unroll
+            for (int r = 0; r < kHalfRows; ++r) rmax[r] = max(rmax[r], __float_as_uint(fabsf(v[r])));
+        }
+        __syncthreads();
+        for (int64_t cb = (int64_t)warp * kGroupsPerWarp; cb < a.ncol_out; cb += ngroups) {
+            const int64_t c = cb + gi;
+            const bool valid = c < a.ncol_out;
+            float acc[kHalfRows];
+#pragma unroll
+            for (int r = 0; r < kHalfRows; ++r) acc[r] = 0.f;
+            if (valid) {
+                const int64_t s0 = a.hls_ptr[2 * c + h], s1 = a.hls_ptr[2 * c + h + 1];
+                const int64_t d0 = a.hld_ptr[2 * c + h], d1 = a.hld_ptr[2 * c + h + 1];
+                const int ls = (int)(s1 - s0), ld = (int)(d1 - d0);
+                for (int cb2 = 0; cb2 < ls; cb2 += kGroup * kListPad) {
+                    const int lc = min(kGroup * kListPad, ls - cb2);
+                    if (kListPad * lig >= lc) break;
+                    int64_t e0, e1;
+                    list_slots(s0, cb2, lc, lig, e0, e1);
+                    const uint4 p0 = __ldg(reinterpret_cast<const uint4 *>(a.hls + e0));
+                    const uint4 p1 = __ldg(reinterpret_cast<const uint4 *>(a.hls + e1));
+                    const uint32_t pk[4] = {p0.x, p0.z, p1.x, p1.z};
+                    const float vv[4] = {__uint_as_float(p0.y), __uint_as_float(p0.w), __uint_as_float(p1.y),
+                                         __uint_as_float(p1.w)};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int64_t jl = (pk[u] ? (int64_t)pk_j(pk[u]) - c0 : 0);
+                        const float4 xa = *reinterpret_cast<const float4 *>(Xa + jl * 4);
+                        const float4 xb = *reinterpret_cast<const float4 *>(Xb + jl * 4);
+                        const float4 ja = *reinterpret_cast<const float4 *>(Ja + (size_t)pk_key(pk[u]) * 4);
+                        const float4 jb = *reinterpret_cast<const float4 *>(Jb + (size_t)pk_key(pk[u]) * 4);
+                        acc[0] += (vv[u] + ja.x) * xa.x;
+                        acc[1] += (vv[u] + ja.y) * xa.y;
+                        acc[2] += (vv[u] + ja.z) * xa.z;
+                        acc[3] += (vv[u] + ja.w) * xa.w;
+                        acc[4] += (vv[u] + jb.x) * xb.x;
+                        acc[5] += (vv[u] + jb.y) * xb.y;
+                        acc[6] += (vv[u] + jb.z) * xb.z;
+                        acc[7] += (vv[u] + jb.w) * xb.w;
+                    }
+                }
+                for (int cb2 = 0; cb2 < ld; cb2 += kGroup * kListPad) {
+                    const int lc = min(kGroup * kListPad, ld - cb2);
+                    if (kListPad * lig >= lc) break;
+                    int64_t e0, e1;
+                    list_slots(d0, cb2, lc, lig, e0, e1);
+                    const uint4 p0 = __ldg(reinterpret_cast<const uint4 *>(a.hld + e0));
+                    const uint4 p1 = __ldg(reinterpret_cast<const uint4 *>(a.hld + e1));
+                    const uint32_t jj[4] = {p0.x, p0.z, p1.x, p1.z};
+                    const float vv[4] = {__uint_as_float(p0.y), __uint_as_float(p0.w), __uint_as_float(p1.y),
+                                         __uint_as_float(p1.w)};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        // padding entries have target 0 and value 0: point them at the staged row 0
+                        const int64_t jl = max((int64_t)jj[u] - c0, (int64_t)0);
+                        const float4 xa = *reinterpret_cast<const float4 *>(Xa + jl * 4);
+                        const float4 xb = *reinterpret_cast<const float4 *>(Xb + jl * 4);
+                        acc[0] += vv[u] * xa.x;
+                        acc[1] += vv[u] * xa.y;
+                        acc[2] += vv[u] * xa.z;
+                        acc[3] += vv[u] * xa.w;
+                        acc[4] += vv[u] * xb.x;
+                        acc[5] += vv[u] * xb.y;
+                        acc[6] += vv[u] * xb.z;
+                        acc[7] += vv[u] * xb.w;
+                    }
+                }
+            }
+#pragma unroll
+            for (int off = kGroup / 2; off > 0; off >>= 1)
+#pragma unroll
+                for (int r = 0; r < kHalfRows; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], off, kGroup);
+            if (valid && lig < nr) {
+                double out = (double)pick<kHalfRows>(acc, lig);
+                const int64_t idx = (r0 + lig) * a.y_rs + c * a.y_cs;
+                if (h == 0) {
+                    if (a.hd) {
+                        const double xc = a.xd64 ? a.xd64[(r0 + lig) * a.ncol + c] : (double)a.X[(r0 + lig) * a.ncol + c];
+                        out += a.hd[idx] * xc;
+                    }
+                    a.Y[idx] = a.accumulate ? a.Y[idx] + out : out;
+                } else {
+                    a.Y[idx] += out;
+                }
+            }
+        }
+    }
+    if (a.rowmax) {  // uniform
+#pragma unroll
+        for (int r = 0; r < kHalfRows; ++r) {
+            const unsigned w = __reduce_max_sync(0xffffffffu, rmax[r]);
+            if (lane == 0) atomicMax(red_h + r, w);
+        }
+        __syncthreads();
+        if (tid < nr) a.rowmax[r0 + tid] = __uint_as_float(red_h[tid]);
+    }
+}
+
+__global__ void __launch_bounds__(Threads<float>::value) row_halves_kernel(const RowArgs<float> a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int64_t r0 = (int64_t)blockIdx.x * kHalfRows; r0 < a.nrow; r0 += (int64_t)gridDim.x * kHalfRows)
+        row_halves(a, r0, smem);
 }
 
 template <typename T>
@@ -660,7 +812,7 @@ __global__ void __launch_bounds__(Threads<T>::value) ab_pass_kernel(const AbArgs
 // The element is hi_sum * 2^L + lo_sum exactly; the row is added to s(ia, :) in FP64 by the CTA
 // that owns the row.
 
-constexpr int kSrcThreads = 1024;
+constexpr int kSrcThreads = 896;
 
 struct AbSrcArgs {
     const float *C;  // [nA][nB] FP32 amplitudes
@@ -1006,6 +1158,20 @@ void set_attrs(int optin)
     SBD_CUDA(cudaFuncSetAttribute(ab_pass_kernel<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
 }
 
+// the mixed 8-row pass over column halves applies when its staged half and tables fit
+bool halves_fit(const RowArgs<float> &a, size_t limit)
+{
+    return a.hls_ptr && a.ncol_out == a.ncol && a.half > 0 && halves_smem(a.half, a.norb) <= limit;
+}
+
+void launch_halves(const RowArgs<float> &a, cudaStream_t s)
+{
+    const int64_t groups = (a.nrow + kHalfRows - 1) / kHalfRows;
+    const int grid = (int)(groups < 65535 ? groups : 65535);
+    row_halves_kernel<<<grid, Threads<float>::value, halves_smem(a.half, a.norb), s>>>(a);
+    SBD_LAUNCH("row_halves_kernel");
+}
+
 template <typename T>
 void launch_row(const RowArgs<T> &a, const PassCfg &p, cudaStream_t s)
 {
@@ -1106,6 +1272,11 @@ void make_args(const Ctx &c, const typename In<T>::type *C, double *S, const dou
     rb.s_ptr = tb.sig_s_ptr;
     rb.d_ptr = tb.sig_d_ptr;
     rb.lists = lists_of<T>(tb);
+    rb.hls_ptr = tb.hs_ptr;
+    rb.hld_ptr = tb.hd_ptr;
+    rb.hls = tb.hs;
+    rb.hld = tb.hd;
+    rb.half = tb.half;
 
     ra = rb;
     ra.X = Ct;
@@ -1121,6 +1292,11 @@ void make_args(const Ctx &c, const typename In<T>::type *C, double *S, const dou
     ra.s_ptr = ta.sig_s_ptr;
     ra.d_ptr = ta.sig_d_ptr;
     ra.lists = lists_of<T>(ta);
+    ra.hls_ptr = ta.hs_ptr;
+    ra.hld_ptr = ta.hd_ptr;
+    ra.hls = ta.hs;
+    ra.hld = ta.hd;
+    ra.half = ta.half;
 
     ab = AbArgs<T>{};
     ab.C = C;
@@ -1152,8 +1328,20 @@ void apply(Ctx &c, const typename In<T>::type *C, double *S, const double *c64, 
     AbArgs<T> ab;
     make_args<T>(c, C, S, c64, Ct, rb, ra, ab);
     if (src) rb.rowmax = c.rowmax;
-    timed(c, base + 1, s, [&] { launch_row<T>(rb, choose(c.nB, n2, sizeof(T), rmax, lim), s); });
-    timed(c, base + 2, s, [&] { launch_row<T>(ra, choose(c.nA, n2, sizeof(T), rmax, lim), s); });
+    if constexpr (std::is_same<T, float>::value) {
+        // 8 rows over column halves where they fit, else 4 rows over the whole row
+        timed(c, base + 1, s, [&] {
+            if (halves_fit(rb, lim)) launch_halves(rb, s);
+            else launch_row<T>(rb, choose(c.nB, n2, sizeof(T), rmax, lim), s);
+        });
+        timed(c, base + 2, s, [&] {
+            if (halves_fit(ra, lim)) launch_halves(ra, s);
+            else launch_row<T>(ra, choose(c.nA, n2, sizeof(T), rmax, lim), s);
+        });
+    } else {
+        timed(c, base + 1, s, [&] { launch_row<T>(rb, choose(c.nB, n2, sizeof(T), rmax, lim), s); });
+        timed(c, base + 2, s, [&] { launch_row<T>(ra, choose(c.nA, n2, sizeof(T), rmax, lim), s); });
+    }
     if constexpr (std::is_same<T, float>::value) {
         if (src) {
             timed(c, base + 3, s, [&] { launch_ab_src(src_args(c, C, S, c.rowmax), c.num_sms, s); });
@@ -1302,8 +1490,18 @@ __global__ void __launch_bounds__(kSrcThreads, 1) ab_src_batch_kernel(const int 
     item_loop(pn, off, args, counter, sa, [&](int64_t li) { src_row(sa, li, smem); });
 }
 
+__global__ void __launch_bounds__(Threads<float>::value) row_halves_batch_kernel(const int *pn, const int64_t *off,
+                                                                               const RowArgs<float> *args,
+                                                                               unsigned long long *counter)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ RowArgs<float> sa;
+    item_loop(pn, off, args, counter, sa, [&](int64_t li) { row_halves(sa, li * kHalfRows, smem); });
+}
+
 size_t batch_smem(size_t elem, int R, int max_strings, int max_norb)
 {
+    if (R == kHalfRows) return halves_smem((max_strings + 1) / 2, max_norb);
     return round16((size_t)max_strings * R * elem) + (size_t)2 * max_norb * max_norb * R * elem;
 }
 
@@ -1366,13 +1564,25 @@ void batch_launch_r(SigmaBatch *b, cudaStream_t s)
     transpose_batch_kernel<E><<<b->grid_t, dim3(32, 8), 0, s>>>(pn, reinterpret_cast<const int64_t *>(d + L.off_t),
                                                                 reinterpret_cast<const TDesc<E> *>(d + L.td));
     SBD_LAUNCH("transpose_batch_kernel");
-    row_batch_kernel<T, R><<<b->grid_pass, kThreads, b->smem, s>>>(
-        pn, reinterpret_cast<const int64_t *>(d + L.off_b), reinterpret_cast<const RowArgs<T> *>(d + L.rb), b->counters);
-    SBD_LAUNCH("row_batch_kernel");
-    row_batch_kernel<T, R><<<b->grid_pass, kThreads, b->smem, s>>>(
-        pn, reinterpret_cast<const int64_t *>(d + L.off_a), reinterpret_cast<const RowArgs<T> *>(d + L.ra),
-        b->counters + 1);
-    SBD_LAUNCH("row_batch_kernel");
+    if constexpr (R == kHalfRows) {
+        row_halves_batch_kernel<<<b->grid_pass, kThreads, b->smem, s>>>(
+            pn, reinterpret_cast<const int64_t *>(d + L.off_b), reinterpret_cast<const RowArgs<float> *>(d + L.rb),
+            b->counters);
+        SBD_LAUNCH("row_halves_batch_kernel");
+        row_halves_batch_kernel<<<b->grid_pass, kThreads, b->smem, s>>>(
+            pn, reinterpret_cast<const int64_t *>(d + L.off_a), reinterpret_cast<const RowArgs<float> *>(d + L.ra),
+            b->counters + 1);
+        SBD_LAUNCH("row_halves_batch_kernel");
+    } else {
+        row_batch_kernel<T, R><<<b->grid_pass, kThreads, b->smem, s>>>(
+            pn, reinterpret_cast<const int64_t *>(d + L.off_b), reinterpret_cast<const RowArgs<T> *>(d + L.rb),
+            b->counters);
+        SBD_LAUNCH("row_batch_kernel");
+        row_batch_kernel<T, R><<<b->grid_pass, kThreads, b->smem, s>>>(
+            pn, reinterpret_cast<const int64_t *>(d + L.off_a), reinterpret_cast<const RowArgs<T> *>(d + L.ra),
+            b->counters + 1);
+        SBD_LAUNCH("row_batch_kernel");
+    }
     if (std::is_same<T, float>::value && b->src) {
         ab_src_batch_kernel<<<b->grid_src, kSrcThreads, b->src_smem, s>>>(
             pn, reinterpret_cast<const int64_t *>(d + L.off_ab), reinterpret_cast<const AbSrcArgs *>(d + L.src),
@@ -1380,21 +1590,29 @@ void batch_launch_r(SigmaBatch *b, cudaStream_t s)
         SBD_LAUNCH("ab_src_batch_kernel");
         return;
     }
-    ab_batch_kernel<T, R><<<b->grid_pass, kThreads, b->smem, s>>>(
-        pn, reinterpret_cast<const int64_t *>(d + L.off_ab), reinterpret_cast<const AbArgs<T> *>(d + L.ab),
-        b->counters + 2);
-    SBD_LAUNCH("ab_batch_kernel");
+    if constexpr (R != kHalfRows) {  // 8 rows per item only come with the column-stationary pass
+        ab_batch_kernel<T, R><<<b->grid_pass, kThreads, b->smem, s>>>(
+            pn, reinterpret_cast<const int64_t *>(d + L.off_ab), reinterpret_cast<const AbArgs<T> *>(d + L.ab),
+            b->counters + 2);
+        SBD_LAUNCH("ab_batch_kernel");
+    }
 }
 
 template <typename T, int R>
 void batch_attrs(SigmaBatch *b)
 {
     constexpr int kThreads = Threads<T>::value;
-    SBD_CUDA(cudaFuncSetAttribute(row_batch_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-    SBD_CUDA(cudaFuncSetAttribute(ab_batch_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-    int occ_row = 0, occ_ab = 0;
-    SBD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_row, row_batch_kernel<T, R>, kThreads, b->smem));
-    SBD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ab, ab_batch_kernel<T, R>, kThreads, b->smem));
+    int occ_row = 0, occ_ab = 1 << 20;
+    if constexpr (R == kHalfRows) {
+        SBD_CUDA(cudaFuncSetAttribute(row_halves_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)b->smem));
+        SBD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_row, row_halves_batch_kernel, kThreads, b->smem));
+    } else {
+        SBD_CUDA(cudaFuncSetAttribute(row_batch_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+        SBD_CUDA(cudaFuncSetAttribute(ab_batch_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+        SBD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_row, row_batch_kernel<T, R>, kThreads, b->smem));
+        SBD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ab, ab_batch_kernel<T, R>, kThreads, b->smem));
+    }
     const int occ = std::max(1, std::min(occ_row, occ_ab));
     int sms = 0;
     SBD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
@@ -1420,6 +1638,7 @@ void sigma_prepare(Ctx &c)
     set_attrs<float>(lim);
     set_attrs<F2>(lim);
     SBD_CUDA(cudaFuncSetAttribute(ab_src_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    SBD_CUDA(cudaFuncSetAttribute(row_halves_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     // max |(pq|rs)| of the FP32 integrals, for the fixed-point scale of the alpha-beta pass
     const int64_t n4 = (int64_t)c.norb * c.norb * c.norb * c.norb;
     unsigned *m = reinterpret_cast<unsigned *>(c.dstat);  // status words are free after create
@@ -1438,6 +1657,16 @@ size_t sigma_batch_smem(sbd_precision prec, int R, int max_strings, int max_norb
     return batch_smem(prec == SBD_MIXED ? 4 : 8, R, max_strings, max_norb);
 }
 
+bool sigma_batch_fits(sbd_precision prec, int R, int max_strings, int max_norb, int device)
+{
+    const size_t lim = sigma_batch_smem_limit(device);
+    if (R == kHalfRows)
+        return prec == SBD_MIXED && max_norb >= 2 && sigma_batch_smem(prec, R, max_strings, max_norb) <= lim &&
+               src_smem(npairs(max_norb), max_strings) <= lim;
+    if (R == 4 && prec != SBD_MIXED) return false;
+    return sigma_batch_smem(prec, R, max_strings, max_norb) <= lim;
+}
+
 size_t sigma_batch_smem_limit(int device)
 {
     int optin = 0;
@@ -1448,8 +1677,9 @@ size_t sigma_batch_smem_limit(int device)
 SigmaBatch *sigma_batch_create(int max_slots, sbd_precision prec, int R, int max_strings, int max_norb, int device)
 {
     if (max_slots < 1) fail(SBD_ERR_INVALID_ARG, "batched sigma needs at least one slot");
-    if (!(R == 1 || R == 2 || (R == 4 && prec == SBD_MIXED)) || prec < SBD_FP64 || prec > SBD_F32X2)
-        fail(SBD_ERR_INVALID_ARG, "rows per work item must be 1, 2 or (mixed only) 4");
+    if (!(R == 1 || R == 2 || ((R == 4 || R == kHalfRows) && prec == SBD_MIXED)) || prec < SBD_FP64 ||
+        prec > SBD_F32X2)
+        fail(SBD_ERR_INVALID_ARG, "rows per work item must be 1, 2 or (mixed only) 4 or 8");
     const size_t smem = sigma_batch_smem(prec, R, max_strings, max_norb);
     if (smem > sigma_batch_smem_limit(device))
         fail(SBD_ERR_UNSUPPORTED, "batched sigma: staged rows do not fit in shared memory");
@@ -1461,6 +1691,11 @@ SigmaBatch *sigma_batch_create(int max_slots, sbd_precision prec, int R, int max
     b->smem = smem;
     b->src_smem = src_smem(npairs(max_norb), max_strings);
     b->src = prec == SBD_MIXED && max_norb >= 2 && b->src_smem <= sigma_batch_smem_limit(device);
+    if (R == kHalfRows && !b->src) {
+        delete b;
+        fail(SBD_ERR_UNSUPPORTED, "batched sigma: 8 rows per item need the column-stationary alpha-beta pass, "
+                                  "whose table and accumulator do not fit shared memory here");
+    }
     b->L = prec == SBD_FP64 ? layout_for<double>(max_slots)
                             : (prec == SBD_F32X2 ? layout_for<F2>(max_slots) : layout_for<float>(max_slots));
     try {
@@ -1475,7 +1710,8 @@ SigmaBatch *sigma_batch_create(int max_slots, sbd_precision prec, int R, int max
             if (R == 2) batch_attrs<F2, 2>(b);
             else batch_attrs<F2, 1>(b);
         } else {
-            if (R == 4) batch_attrs<float, 4>(b);
+            if (R == kHalfRows) batch_attrs<float, kHalfRows>(b);
+            else if (R == 4) batch_attrs<float, 4>(b);
             else if (R == 2) batch_attrs<float, 2>(b);
             else batch_attrs<float, 1>(b);
         }
@@ -1510,7 +1746,8 @@ void sigma_batch_launch(SigmaBatch *b, cudaStream_t s)
         if (b->R == 2) batch_launch_r<F2, 2>(b, s);
         else batch_launch_r<F2, 1>(b, s);
     } else {
-        if (b->R == 4) batch_launch_r<float, 4>(b, s);
+        if (b->R == kHalfRows) batch_launch_r<float, kHalfRows>(b, s);
+        else if (b->R == 4) batch_launch_r<float, 4>(b, s);
         else if (b->R == 2) batch_launch_r<float, 2>(b, s);
         else batch_launch_r<float, 1>(b, s);
     }

@@ -352,21 +352,19 @@ __global__ void ediag_kernel(const uint64_t *S, int64_t n, int norb, const doubl
 }
 
 // Sigma order of each source's list.  The list is padded with empty slots to a multiple of
-// kListPad and read in chunks of up to 32 slots by an 8-lane group: in a chunk of Lc slots lane l
-// fetches slots {2l, 2l+1} and {Lc/2 + 2l, Lc/2 + 2l + 1} (each of the group's two loads reads a
-// contiguous run), and the u-th 128-bit shared-memory phase gathers slot (u/2)*(Lc/2) + 2l + u%2 of
-// every lane l.  Entries are first ranked as rounds "rank 0 of every target residue mod 8, rank 1 of
-// every residue, ...", so that consecutive entries in that order have distinct residues where the
+// kListPad and laid out for 16-byte loads: lane l of an 8-lane group fetches slots 4l..4l+3 of
+// each 32-slot chunk, and one 128-bit shared-memory phase gathers slot 4l+u of every lane.
+// Entries are first ranked as rounds "rank 0 of every target residue mod 8, rank 1 of every
+// residue, ...", so that consecutive entries in that order have distinct residues where the
 // residue counts allow; each phase then receives a run of consecutive positions.
-// round-order position q of a list of Lp slots -> slot: with m = Lc/4 lanes in the chunk, position
-// m*u + l goes to the slot phase u gathers for lane l, so each phase reads m consecutive positions
+// round-order position q of a list of Lp slots -> slot: in a chunk of Lc slots (32, or what is left of
+// a short list) m = Lc/4 lanes each fetch 4 slots, and phase u gathers slot 4*l + u of every lane l;
+// position m*u + l goes to slot 4*l + u, so each phase reads m consecutive round-order positions
 __device__ __forceinline__ int slot_of(int q, int Lp)
 {
     const int chunk = q / 32, within = q % 32;
-    const int lc = min(32, Lp - chunk * 32);
-    const int m = lc / 4;
-    const int u = within / m, l = within % m;
-    return chunk * 32 + (u / 2) * (lc / 2) + 2 * l + (u % 2);
+    const int m = min(32, Lp - chunk * 32) / 4;
+    return chunk * 32 + 4 * (within % m) + within / m;
 }
 
 // Singles lists, where the gathers read two tables: staged amplitudes by target j and coefficient
@@ -517,6 +515,34 @@ __global__ void src_slice_order_kernel(const uint32_t *__restrict__ item_in, con
         item_out[s * 32 + rank] = it;
         const int64_t base = s * 32 * kSrcItem;
         for (int i = 0; i < kSrcItem; ++i) ent_out[base + 32 * i + rank] = ent_in[base + 32 * i + lane];
+    }
+}
+
+// Split of each source list at target `half`: ptr2[2i] = start of list i, ptr2[2i+1] = its first
+// entry with target >= half (targets ascend in the canonical lists), ptr2[2n] = end of the last list
+__global__ void half_split_kernel(const int64_t *__restrict__ ptr, const int32_t *__restrict__ tgt, int64_t n,
+                                  int64_t half, int64_t *ptr2)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = ptr[i], hi = ptr[i + 1];
+        ptr2[2 * i] = lo;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            if (tgt[mid] < half) lo = mid + 1;
+            else hi = mid;
+        }
+        ptr2[2 * i + 1] = lo;
+        if (i == n - 1) ptr2[2 * n] = ptr[n];
+    }
+}
+
+// out[o] = (key[perm[o]], FP32 of val[perm[o]]), zeros for padding
+__global__ void gather_pair_kernel(const int64_t *__restrict__ perm, int64_t m, const uint32_t *__restrict__ key,
+                                   const double *__restrict__ val, uint2 *out)
+{
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < m; o += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = perm[o];
+        out[o] = e >= 0 ? make_uint2(key[e], __float_as_uint(__double2float_rn(val[e]))) : make_uint2(0u, 0u);
     }
 }
 
@@ -709,6 +735,42 @@ void build_tables(Ctx &c, int spin)
         SBD_LAUNCH("split_kernel(doubles)");
     }
     dfree(c, perm);
+    // mixed-sigma lists split at the middle of the set (row passes over column halves)
+    {
+        t.half = (n + 1) / 2;
+        int64_t *ptr2 = dalloc_n<int64_t>(c, 2 * (size_t)n + 1);
+        int64_t *cnt2 = dalloc_n<int64_t>(c, 2 * (size_t)n);
+        for (int kind = 0; kind < 2; ++kind) {
+            const int64_t *ptr = kind == 0 ? t.s_ptr : t.d_ptr;
+            const int32_t *tgt = kind == 0 ? t.s_j : t.d_j;
+            int64_t *&hptr = kind == 0 ? t.hs_ptr : t.hd_ptr;
+            uint2 *&hout = kind == 0 ? t.hs : t.hd;
+            half_split_kernel<<<blocks_for(n, 256), 256, 0, c.stream>>>(ptr, tgt, n, t.half, ptr2);
+            SBD_LAUNCH("half_split_kernel");
+            hptr = dalloc_n<int64_t>(c, 2 * (size_t)n + 1);
+            padded_count_kernel<<<blocks_for(2 * n, 256), 256, 0, c.stream>>>(ptr2, 2 * n, cnt2);
+            SBD_LAUNCH("padded_count_kernel(halves)");
+            scan_kernel<<<1, 1024, 0, c.stream>>>(cnt2, 2 * n, hptr);
+            SBD_LAUNCH("scan_kernel(halves)");
+            int64_t m = 0;
+            SBD_CUDA(cudaMemcpyAsync(&m, hptr + 2 * n, sizeof(int64_t), cudaMemcpyDeviceToHost, c.stream));
+            SBD_CUDA(cudaStreamSynchronize(c.stream));
+            hout = dalloc_n<uint2>(c, (size_t)std::max<int64_t>(m, 1));
+            if (m) {
+                int64_t *hperm = dalloc_n<int64_t>(c, (size_t)m);
+                sigma_order_kernel<<<blocks_for(2 * n, 128), 128, 0, c.stream>>>(ptr2, hptr, 2 * n, tgt,
+                                                                                  kind == 0 ? t.s_pk : nullptr, hperm);
+                SBD_LAUNCH("sigma_order_kernel(halves)");
+                gather_pair_kernel<<<blocks_for(m, 256, 16384), 256, 0, c.stream>>>(
+                    hperm, m, kind == 0 ? t.s_pk : reinterpret_cast<const uint32_t *>(t.d_j),
+                    kind == 0 ? t.s_v64 : t.d_v64, hout);
+                SBD_LAUNCH("gather_pair_kernel(halves)");
+                dfree(c, hperm);
+            }
+        }
+        dfree(c, cnt2);
+        dfree(c, ptr2);
+    }
     // source-major singles: items of at most kSrcItem singles, 32 items per slice
     {
         int64_t *ioff = dalloc_n<int64_t>(c, n + 1);
