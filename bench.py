@@ -560,6 +560,96 @@ def run_serve(args):
     return 0
 
 
+def run_shard(args):
+    """One instance alpha-row-sharded over the ranks (paper Sec. III): every rank holds the tables
+    and its rows of every vector; sigma passes the C blocks around the ring of ranks
+    (shard.DistRing: NCCL point-to-point into the library's receive buffers, double buffered), and
+    the Davidson dot products are summed over the group.  Total work is fixed as the rank count
+    grows ("scaling": "strong"); at one rank it is the sharded code path with a single block."""
+    import torch
+
+    from paper_2601_16637_gb300 import binding as B
+    from paper_2601_16637_gb300 import shard as S
+    from paper_2601_16637_gb300 import workloads as W
+
+    rank, local_rank, world = env_rank()
+    world = max(world, 1)
+    torch.cuda.set_device(local_rank)
+    import torch.distributed as dist
+
+    if world == 1:  # a single rank started without torchrun
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        if "MASTER_PORT" not in os.environ:
+            import socket
+
+            with socket.socket() as so:
+                so.bind(("127.0.0.1", 0))
+                os.environ["MASTER_PORT"] = str(so.getsockname()[1])
+        os.environ.setdefault("RANK", "0")
+        os.environ.setdefault("WORLD_SIZE", "1")
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank), init_method="env://")
+    B.load(build_if_missing=True)
+    wl = W.config(args.workload)
+    prec = wl.precision
+    stream = torch.cuda.current_stream()
+    alloc = B._TorchAllocator()
+    h_d = torch.from_numpy(wl.h).cuda()
+    eri_d = torch.from_numpy(wl.eri).cuda()
+    A_d = torch.from_numpy(wl.A.view(np.int64)).cuda()
+    B_d = torch.from_numpy(wl.B.view(np.int64)).cuda()
+    ring = S.DistRing()
+    comm = ring.comm()
+
+    def step():
+        o = B.sbd_default_options()
+        o.max_subspace = wl.max_subspace
+        o.alloc, o.free = alloc.alloc, alloc.free
+        handle = B.sbd_create(wl.norb, wl.nalpha, wl.nbeta, h_d, eri_d, A_d, B_d, o, stream)
+        nA, nB = B.sbd_dims(handle)
+        bounds = S.row_blocks(nA, world)
+        rows = (bounds[rank + 1] - bounds[rank]) * nB
+        vec = torch.empty((wl.nroots, rows), dtype=torch.float64, device="cuda")
+        e = np.empty(wl.nroots)
+        r = np.empty(wl.nroots)
+        rc, rep = B.sbd_davidson_sharded(handle, bounds, comm, wl.nroots, wl.tol, prec, e, vec, r)
+        B.sbd_destroy(handle)
+        return e, r, rep.as_dict()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = B.sbd_launch_count()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t0 = time.perf_counter()
+    reports, energies, resid = [], None, None
+    for _ in range(args.steps):
+        energies, resid, rep = step()
+        reports.append(rep)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    elapsed = max_over_ranks(time.perf_counter() - t0, world)
+    clk = clocks.stop()
+    n_sigma = sum(r["sigma_fp64"] + r["sigma_mixed"] for r in reports)
+    value = float(wl.ndets) * n_sigma / elapsed
+    if rank == 0:
+        cfg = workload_config(wl, prec)
+        cfg["step"] = "sbd_create + sbd_davidson_sharded + sbd_destroy (one solve, alpha rows sharded over the ranks)"
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None,
+                "dtype": "f32+f32x2+f64" if prec == "mixed" else "f64", "data": "synthetic", "config": cfg,
+                "parallelism": f"alpha-row sharding over {world} rank(s), ring exchange of C blocks",
+                "solves_per_s": args.steps / elapsed, "energy_Ha": float(energies[0]), "residual": float(resid[0]),
+                "gpu_launches": int(B.sbd_launch_count() - launches0), "clocks": clk, "last_report": reports[-1]}
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -567,6 +657,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg3")
+    ap.add_argument("--mode", default="replicas", choices=["replicas", "shard"],
+                    help="replicas: each GPU solves its own instance; shard: one instance over all ranks")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample budget for cpu_baseline")
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--no-fp64-compare", action="store_true")
@@ -596,6 +688,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.mode == "shard":
+        return run_shard(args)
 
     import torch
 

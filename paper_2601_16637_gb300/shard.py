@@ -186,25 +186,38 @@ class ThreadRing:
 
 class DistRing:
     """Communicator over a torch.distributed process group (one process per GPU): allreduce of
-    host doubles through a tensor of the group's device, ring exchange with isend/irecv of device
-    buffers (NCCL)."""
+    host doubles through a tensor of the group's device, ring exchange of the library's buffers.
 
-    def __init__(self, group=None):
+    buffers="device" (what sbd_davidson_sharded passes): with NCCL the device buffers are sent and
+    received in place (isend/irecv); with gloo they are staged through host memory.  buffers="host":
+    the pointers are host memory and travel as CPU tensors (gloo)."""
+
+    def __init__(self, group=None, buffers: str = "device"):
         import torch.distributed as dist
 
+        if buffers not in ("device", "host"):
+            raise ValueError("buffers must be 'device' or 'host'")
         self.group = group
+        self.buffers = buffers
         self.rank = dist.get_rank(group)
         self.world = dist.get_world_size(group)
         self._keep = []
 
     def comm(self):
+        import ctypes
+
         import numpy as np
         import torch
         import torch.distributed as dist
 
         from . import binding as B
 
-        dev = "cuda" if dist.get_backend(self.group) == "nccl" else "cpu"
+        nccl = dist.get_backend(self.group) == "nccl"
+        dev = "cuda" if nccl else "cpu"
+        nxt, prv = (self.rank + 1) % self.world, (self.rank - 1) % self.world
+
+        def host_view(ptr, nbytes):
+            return torch.from_numpy(np.ctypeslib.as_array((ctypes.c_uint8 * int(nbytes)).from_address(int(ptr))))
 
         def allreduce(ctx, buf, n):
             try:
@@ -218,11 +231,21 @@ class DistRing:
 
         def ring(ctx, send, send_bytes, recv, recv_bytes, stream):
             try:
-                reqs = [dist.isend(device_view(send, send_bytes), (self.rank + 1) % self.world, group=self.group),
-                        dist.irecv(device_view(recv, recv_bytes), (self.rank - 1) % self.world, group=self.group)]
+                if self.buffers == "host":
+                    s_t, r_t = host_view(send, send_bytes), host_view(recv, recv_bytes)
+                elif nccl:
+                    s_t, r_t = device_view(send, send_bytes), device_view(recv, recv_bytes)
+                else:  # gloo: stage the device buffers through host memory
+                    torch.cuda.synchronize()
+                    s_t = device_view(send, send_bytes).cpu()
+                    r_t = torch.empty(int(recv_bytes), dtype=torch.uint8)
+                reqs = [dist.isend(s_t, nxt, group=self.group), dist.irecv(r_t, prv, group=self.group)]
                 for q in reqs:
                     q.wait()
-                torch.cuda.synchronize()
+                if self.buffers == "device":
+                    if not nccl:
+                        device_view(recv, recv_bytes).copy_(r_t)
+                    torch.cuda.synchronize()
                 return 0
             except Exception:
                 return 1

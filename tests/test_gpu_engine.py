@@ -229,3 +229,38 @@ def test_engine_reports_a_failing_job_and_finishes_the_others(B, alone):
         e.release(jb)
         with pytest.raises(B.SbdError):
             e.result(jb)
+
+
+def test_engine_norb58_job_alone_and_in_a_mix(B, oracle_mod):
+    # the top of the serving configuration's orbital range (norb 58, 19+19 electrons) with small
+    # string sets: same result alone and beside other jobs, equal to the single-instance FP64 solve,
+    # and an eigenvector whose residual is small on rows of the oracle's sigma
+    big = W.make("n58", 58, 19, 19, 300, 260, 0.35, seed=58)
+    others = _small_jobs()[1:3]
+    opts = dict(max_slots=4, max_subspace=12, max_norb=64, max_strings=2000)
+    with B.Engine(**opts) as e:
+        j = e.submit(big, tol=TOL, tol_energy=TOL_E, keep_vector=True)
+        e.run()
+        ra = e.result(j)
+        va = e.vector(j, ra["ndets"])
+    assert ra["status"] == 0, ra
+    with B.Engine(**opts) as e:
+        ids = [e.submit(w, tol=TOL, tol_energy=TOL_E) for w in others]
+        j = e.submit(big, tol=TOL, tol_energy=TOL_E, keep_vector=True)
+        e.run()
+        rm = e.result(j)
+        assert all(e.result(i)["status"] == 0 for i in ids)
+        assert rm["energy"] == ra["energy"] and rm["iterations"] == ra["iterations"]
+        assert np.array_equal(e.vector(j, rm["ndets"]), va)
+    with B.SBD.from_workload(big) as g:
+        s = g.davidson(1, 1e-9, "fp64")
+        assert s.status == 0
+        assert abs(ra["energy"] - s.energies[0]) < 1e-7
+        assert abs(float(np.dot(s.vectors[0].cpu().numpy(), va))) > 1 - 1e-6
+    o = oracle_mod.Oracle.from_workload(big)
+    rows = np.random.default_rng(58).choice(big.ndets, 40, replace=False)
+    hv = o.sigma_rows(va[None, :], rows)[0]
+    r = hv - ra["energy"] * va[rows]
+    o.close()
+    # |r_i| <= ||r|| <= TOL for every row of the exact residual vector
+    assert np.abs(r).max() <= 2 * TOL

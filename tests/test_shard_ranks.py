@@ -157,3 +157,45 @@ def test_dist_ring_allreduce_callback_over_gloo_ranks():
         assert rc == 0 and crank == rank and cworld == world
         assert np.allclose(got, expect, rtol=1e-15, atol=0)
         assert got == res[0][4]  # every rank holds the same bits
+
+
+def _dist_ring_exchange_worker(rank, world, port, q):
+    import ctypes
+
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    from paper_2601_16637_gb300 import shard as S
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    comm = S.DistRing(buffers="host").comm()
+    # blocks of unequal size, as row_blocks gives when the rows do not divide evenly
+    sizes = [40 + 8 * r for r in range(world)]
+    send = np.arange(sizes[rank], dtype=np.uint8) * 3 + rank
+    recv = np.zeros(sizes[(rank - 1) % world], dtype=np.uint8)
+    rc = comm.ring_exchange(None, ctypes.c_void_p(send.ctypes.data), send.nbytes,
+                            ctypes.c_void_p(recv.ctypes.data), recv.nbytes, None)
+    q.put((rank, rc, recv.tolist()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_dist_ring_exchange_callback_over_gloo_ranks(world):
+    # the ring callback handed to sbd_davidson_sharded, on host buffers over gloo: every rank
+    # receives exactly the block of the rank before it (blocks of different sizes)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dist_ring_exchange_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(world))
+    sizes = [40 + 8 * r for r in range(world)]
+    for rank, rc, got in res:
+        prv = (rank - 1) % world
+        assert rc == 0
+        assert got == (np.arange(sizes[prv], dtype=np.uint8) * 3 + prv).tolist()
