@@ -309,7 +309,7 @@ def kernel_source_digest() -> str:
     end = src.index("\n}\n", src.index("__global__ void __launch_bounds__(kSrcThreads, 1) ab_src_kernel(")) + 3
     tab = open(os.path.join(csrc, "tables.cu")).read()
     t0 = tab.index("__global__ void src_count_kernel(")
-    t1 = tab.index("\n}\n", tab.index("__global__ void src_slice_order_kernel(")) + 3
+    t1 = tab.index("\n}\n", tab.index("__global__ void src_entry_order_kernel(")) + 3
     return hashlib.sha256((src[start:end] + tab[t0:t1]).encode()).hexdigest()[:16]
 
 

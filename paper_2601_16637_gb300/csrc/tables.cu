@@ -546,6 +546,45 @@ __global__ void gather_pair_kernel(const int64_t *__restrict__ perm, int64_t m, 
     }
 }
 
+// Order of the entries inside the items of each slice: in round i every lane of the warp adds the
+// dot product of its item's i-th entry into the row accumulator at the entry's target (32-bit shared
+// atomics, bank = target mod 32).  Round by round, each lane takes, of its entries not yet placed,
+// one whose bank no earlier lane of that round has taken (the first such), else its first remaining
+// entry, so the 32 atomics of a round hit distinct banks where the slice's targets allow.  Any order
+// gives the same sums; one thread per slice.
+__global__ void src_entry_order_kernel(const uint32_t *__restrict__ item, uint32_t *ent, int64_t nsl)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nsl; s += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t *e = ent + s * 32 * kSrcItem;
+        uint32_t loc[32][kSrcItem];
+        int cnt[32];
+        unsigned left[32];
+        for (int l = 0; l < 32; ++l) {
+            cnt[l] = (int)(item[s * 32 + l] >> kSrcPairShift);
+            left[l] = (1u << cnt[l]) - 1u;
+            for (int i = 0; i < kSrcItem; ++i) loc[l][i] = e[32 * i + l];
+        }
+        for (int i = 0; i < kSrcItem; ++i) {
+            unsigned used = 0u;
+            for (int l = 0; l < 32; ++l) {
+                if (i >= cnt[l]) continue;
+                int pick = -1;
+                for (int x = 0; x < cnt[l]; ++x) {
+                    if (!((left[l] >> x) & 1u)) continue;
+                    if (pick < 0) pick = x;
+                    if (!((used >> (loc[l][x] & 31u)) & 1u)) {
+                        pick = x;
+                        break;
+                    }
+                }
+                left[l] &= ~(1u << pick);
+                used |= 1u << (loc[l][pick] & 31u);
+                e[32 * i + l] = loc[l][pick];
+            }
+        }
+    }
+}
+
 // (key, FP32 value) pairs for single 8-byte loads in the mixed sigma
 __global__ void pair_kernel(const uint32_t *__restrict__ key, const double *__restrict__ val, uint2 *out, int64_t n)
 {
@@ -801,6 +840,8 @@ void build_tables(Ctx &c, int spin)
         dfree(c, t.src_ent);
         t.src_item = item2;
         t.src_ent = ent2;
+        src_entry_order_kernel<<<blocks_for(nsl, 64), 64, 0, c.stream>>>(t.src_item, t.src_ent, nsl);
+        SBD_LAUNCH("src_entry_order_kernel");
     }
     t.ediag = dalloc_n<double>(c, n);
     ediag_kernel<<<blocks_for(n, 128), 128, 0, c.stream>>>(t.strings, n, norb, c.h64, c.eri64, t.ediag);
