@@ -111,6 +111,46 @@ __global__ void __launch_bounds__(kBlas) mdot_partial(const double *__restrict__
     }
 }
 
+// The same sums in FP32 pairs (48-bit operands, FP32 pipe; one FP64 rounding per block sum), for
+// the pair-arithmetic solves.  blockIdx.y picks a chunk of kPairChunk basis vectors, so that the
+// accumulators stay few (the FP64 form is bound by the FP64 pipe, one multiply-add per element and
+// basis vector; this one runs near the HBM rate).  With NORM, chunk 0 also sums y^2 in FP64.
+constexpr int kPairChunk = 8;
+template <bool NORM>
+__global__ void __launch_bounds__(kBlas) mdot_pair_partial(const double *__restrict__ X, int64_t ldx, int k,
+                                                           const double *__restrict__ y, int64_t N, double *partial)
+{
+    __shared__ double red[kBlas / 32];
+    const int a0 = blockIdx.y * kPairChunk;
+    const int kc = min(kPairChunk, k - a0);
+    X += a0 * ldx;
+    const bool nrm = NORM && blockIdx.y == 0;
+    F2 acc[kPairChunk];
+#pragma unroll
+    for (int a = 0; a < kPairChunk; ++a) acc[a] = F2(0.f);
+    double an = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kBlas + threadIdx.x; i < N; i += (int64_t)gridDim.x * kBlas) {
+        const double yi = y[i];
+        if (nrm) an += yi * yi;
+        const F2 ys = f2_split(yi);
+        double x[kPairChunk];
+#pragma unroll
+        for (int u = 0; u < kPairChunk; ++u) x[u] = u < kc ? X[u * ldx + i] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kPairChunk; ++u) f2_mac(acc[u], f2_split(x[u]), ys);
+    }
+#pragma unroll
+    for (int a = 0; a < kPairChunk; ++a)
+        if (a < kc) {  // kc is uniform over the block
+            const double s = block_sum(f2_value(acc[a]), red);
+            if (threadIdx.x == 0) partial[blockIdx.x * kPart + a0 + a] = s;
+        }
+    if (nrm) {
+        const double s = block_sum(an, red);
+        if (threadIdx.x == 0) partial[blockIdx.x * kPart + kDotMax] = s;
+    }
+}
+
 // out1[a*st1] (and out2[a*st2] when given) = sum_b partial[b][a] for a < k;
 // slot kDotMax (the norm) goes to *norm2 when given.  Fixed summation order.
 __global__ void mdot_final(const double *partial, int nblocks, int k, double *out1, int64_t st1, double *out2,
@@ -129,27 +169,41 @@ __global__ void mdot_final(const double *partial, int nblocks, int k, double *ou
     }
 }
 
-// y -= sum_a coef[a] X[a] (a < k <= kMaxSub); with NORM, partial[b*kPart + kDotMax] = sum of the new y^2
-template <bool NORM>
+// y -= sum_a coef[a] X[a] (a < k <= kMaxSub); with NORM, partial[b*kPart + kDotMax] = sum of the new y^2.
+// PAIR: the sum over a in FP32 pairs, subtracted from y in FP64.
+template <bool NORM, bool PAIR>
 __global__ void __launch_bounds__(kBlas) maxpy_kernel(const double *__restrict__ X, int64_t ldx, int k,
                                                       const double *__restrict__ coef, double *y, int64_t N,
                                                       double *partial)
 {
     __shared__ double cs[kMaxSub];
     __shared__ double red[kBlas / 32];
-    for (int a = threadIdx.x; a < kMaxSub; a += kBlas) cs[a] = a < k ? coef[a] : 0.0;
+    F2 *cs2 = reinterpret_cast<F2 *>(cs);  // PAIR: the coefficients as pairs (8 bytes each)
+    for (int a = threadIdx.x; a < kMaxSub; a += kBlas) {
+        const double v = a < k ? coef[a] : 0.0;
+        if (PAIR) cs2[a] = f2_split(v);
+        else cs[a] = v;
+    }
     __syncthreads();
     double an = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)kBlas + threadIdx.x; i < N; i += (int64_t)gridDim.x * kBlas) {
-        double s = 0.0;
+        using Acc = typename std::conditional<PAIR, F2, double>::type;
+        Acc s = Acc(0.f);
         for (int a0 = 0; a0 < k; a0 += kLoad) {
             double x[kLoad];
 #pragma unroll
             for (int u = 0; u < kLoad; ++u) x[u] = (a0 + u < k) ? X[(a0 + u) * ldx + i] : 0.0;
 #pragma unroll
-            for (int u = 0; u < kLoad; ++u) s += cs[min(a0 + u, kMaxSub - 1)] * x[u];
+            for (int u = 0; u < kLoad; ++u) {
+                const int a = min(a0 + u, kMaxSub - 1);
+                if constexpr (PAIR) f2_mac(s, cs2[a], f2_split(x[u]));
+                else s += cs[a] * x[u];
+            }
         }
-        const double yn = y[i] - s;
+        double sv;
+        if constexpr (PAIR) sv = f2_value(s);
+        else sv = s;
+        const double yn = y[i] - sv;
         y[i] = yn;
         if (NORM) an += yn * yn;
     }
@@ -252,6 +306,102 @@ __global__ void __launch_bounds__(kBlas) combine_kernel(const double *__restrict
                 if (threadIdx.x == 0) partial[blockIdx.x * kPart + j] = s;
             }
     }
+}
+
+// The Ritz step of one root in FP32 pairs (combine_kernel<true, 1, true>) and, from the same loaded
+// and split basis values, the first Gram-Schmidt projections of the new correction:
+// partial2[b*kPart + a] = sum over block b of X[a] . tc (a < k <= KB), partial2[b*kPart + kDotMax] =
+// tc . tc.  A block works on tiles of kBlas elements: each thread parks its element's split X[a]
+// and its split tc in shared memory ([KB + 1][kBlas] pairs, dynamic), then warp w sums the products
+// of basis vectors a = w, w + 8, ... over the tile (a few accumulators per thread instead of KB, so
+// three blocks fit an SM).  A separate pass would read the basis from HBM again.
+template <int KB>
+__global__ void __launch_bounds__(kBlas, 3) ritz_dots_kernel(const double *__restrict__ X,
+                                                             const double *__restrict__ H, int64_t ldx, int k,
+                                                             const double *__restrict__ Y, double *out, double *hout,
+                                                             const double *__restrict__ theta,
+                                                             const double *__restrict__ hd, double delta, double *tc,
+                                                             double *partial, double *partial2, int64_t N)
+{
+    static_assert(KB % (kBlas / 32) == 0, "basis vectors are dealt to the warps in equal numbers");
+    constexpr int kWarps = kBlas / 32, kPerWarp = KB / kWarps;
+    extern __shared__ F2 xsh[];  // [KB][kBlas] split basis values, then [kBlas] split corrections
+    F2 *tsh = xsh + KB * kBlas;
+    __shared__ F2 ys2[KB];
+    __shared__ double red[kBlas / 32];
+    __shared__ double wsum[KB];
+    for (int a = threadIdx.x; a < KB; a += kBlas) ys2[a] = a < k ? f2_split(Y[a * kMaxSub]) : F2(0.f);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double th = theta[0];
+    double racc = 0.0, nacc = 0.0;
+    F2 dacc[kPerWarp];
+#pragma unroll
+    for (int j = 0; j < kPerWarp; ++j) dacc[j] = F2(0.f);
+    for (int64_t t0 = (int64_t)blockIdx.x * kBlas; t0 < N; t0 += (int64_t)gridDim.x * kBlas) {  // uniform
+        const int64_t i = t0 + threadIdx.x;
+        const bool valid = i < N;
+        F2 u(0.f), hu(0.f);
+#pragma unroll 2
+        for (int a0 = 0; a0 < k; a0 += kLoad / 2) {
+            double x[kLoad / 2], h[kLoad / 2];
+#pragma unroll
+            for (int q = 0; q < kLoad / 2; ++q) {
+                const bool ok = a0 + q < k && valid;
+                x[q] = ok ? X[(a0 + q) * ldx + i] : 0.0;
+                h[q] = ok ? H[(a0 + q) * ldx + i] : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < kLoad / 2; ++q) {
+                const int a = a0 + q;
+                if (a < k) {
+                    const F2 xs = f2_split(x[q]);
+                    xsh[a * kBlas + threadIdx.x] = xs;
+                    f2_mac(u, ys2[a], xs);
+                    f2_mac(hu, ys2[a], f2_split(h[q]));
+                }
+            }
+        }
+        F2 ts(0.f);
+        if (valid) {
+            const double uj = f2_value(u), huj = f2_value(hu);
+            out[i] = uj;
+            hout[i] = huj;
+            const double r = huj - th * uj;
+            racc += r * r;
+            const double t = r * precond_factor(hd[i] - th, delta);
+            tc[i] = t;
+            nacc += t * t;
+            ts = f2_split(t);
+        }
+        tsh[threadIdx.x] = ts;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kPerWarp; ++j) {
+            const int a = warp + kWarps * j;
+            if (a < k)
+#pragma unroll
+                for (int e = lane; e < kBlas; e += 32) f2_mac(dacc[j], xsh[a * kBlas + e], tsh[e]);
+        }
+        __syncthreads();  // the tile's shared memory is rewritten next
+    }
+    const double sr = block_sum(racc, red);
+    if (threadIdx.x == 0) partial[blockIdx.x * kPart] = sr;
+#pragma unroll
+    for (int j = 0; j < kPerWarp; ++j) {
+        double v = f2_value(dacc[j]);
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) wsum[warp + kWarps * j] = v;
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < k; a += kBlas) partial2[blockIdx.x * kPart + a] = wsum[a];
+    const double sn = block_sum(nacc, red);
+    if (threadIdx.x == 0) partial2[blockIdx.x * kPart + kDotMax] = sn;
+}
+template <int KB>
+constexpr int ritz_dots_smem()
+{
+    return (KB + 1) * kBlas * (int)sizeof(F2);
 }
 
 // partial[b*kPart + j] = sum over block b of (HU[j] - theta[j] U[j])^2, j < m <= kRitzMax
@@ -387,9 +537,10 @@ struct Work {
     int64_t N;      // local vector length (this rank's rows in a sharded solve)
     int64_t off;    // global index of local element 0
     ShardCtx *sh;   // null: one process holds the whole vectors
-    bool pair = false;  // Ritz combinations (combine_kernel) summed in FP32 pairs
+    bool pair = false;  // Ritz combinations, basis dot products and updates summed in FP32 pairs
     int grid;
     double *partial = nullptr;  // [grid][kPart]
+    double *partial2 = nullptr; // [grid][kPart]: projections from the fused Ritz pass
     double *dscal = nullptr;    // kMaxSub + 1 doubles: local dot products before the sum over ranks
     double *pv = nullptr;
     int64_t *pi = nullptr;
@@ -419,12 +570,14 @@ struct Work {
     // out1[a*st1] (and out2[a*st2]) = X[a] . y for a < k; with norm2, also y . y.  In a sharded solve
     // the local sums go to a contiguous scratch first, are summed over the ranks, then written out
     // (out1 and out2 may share an entry).
+    // With pair, the products are summed in FP32 pairs unless fp64 asks for FP64 arithmetic.
     void dots(const double *X, int64_t ldx, int k, const double *y, double *out1, int64_t st1,
-              double *out2 = nullptr, int64_t st2 = 0, double *norm2 = nullptr)
+              double *out2 = nullptr, int64_t st2 = 0, double *norm2 = nullptr, bool fp64 = false)
     {
+        const bool pr = pair && !fp64;
         if (sh && sh->world > 1) {
             double *tmp = dscal;  // kMaxSub + 1 doubles
-            local_dots(X, ldx, k, y, tmp, 1, nullptr, 0, norm2 ? tmp + k : nullptr);
+            local_dots(X, ldx, k, y, tmp, 1, nullptr, 0, norm2 ? tmp + k : nullptr, pr);
             std::vector<double> h((size_t)k + 1, 0.0);
             const int n = k + (norm2 ? 1 : 0);
             SBD_CUDA(cudaMemcpyAsync(h.data(), tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
@@ -441,26 +594,36 @@ struct Work {
             SBD_CUDA(cudaStreamSynchronize(s));  // h leaves scope
             return;
         }
-        local_dots(X, ldx, k, y, out1, st1, out2, st2, norm2);
+        local_dots(X, ldx, k, y, out1, st1, out2, st2, norm2, pr);
+    }
+    template <bool NORM, bool PAIR>
+    void launch_mdot(const double *Xa, int64_t ldx, int kb, const double *y)
+    {
+        if (PAIR) {
+            const dim3 g(grid, std::max(1, (kb + kPairChunk - 1) / kPairChunk));
+            mdot_pair_partial<NORM><<<g, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+            SBD_LAUNCH("mdot_pair_partial");
+            return;
+        }
+        if (kb <= 8) mdot_partial<NORM, 8><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+        else if (kb <= 16) mdot_partial<NORM, 16><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+        else mdot_partial<NORM, kDotMax><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+        SBD_LAUNCH("mdot_partial");
     }
     void local_dots(const double *X, int64_t ldx, int k, const double *y, double *out1, int64_t st1,
-                    double *out2, int64_t st2, double *norm2)
+                    double *out2, int64_t st2, double *norm2, bool pr)
     {
         for (int a0 = 0; a0 < k || (a0 == 0 && norm2); a0 += kDotMax) {
             const int kb = std::min(kDotMax, k - a0);
             const bool nrm = norm2 && a0 == 0;
             const double *Xa = X + a0 * ldx;
-            if (kb <= 8) {
-                if (nrm) mdot_partial<true, 8><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
-                else mdot_partial<false, 8><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
-            } else if (kb <= 16) {
-                if (nrm) mdot_partial<true, 16><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
-                else mdot_partial<false, 16><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+            if (nrm) {
+                if (pr) launch_mdot<true, true>(Xa, ldx, kb, y);
+                else launch_mdot<true, false>(Xa, ldx, kb, y);
             } else {
-                if (nrm) mdot_partial<true, kDotMax><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
-                else mdot_partial<false, kDotMax><<<grid, kBlas, 0, s>>>(Xa, ldx, kb, y, N, partial);
+                if (pr) launch_mdot<false, true>(Xa, ldx, kb, y);
+                else launch_mdot<false, false>(Xa, ldx, kb, y);
             }
-            SBD_LAUNCH("mdot_partial");
             mdot_final<<<1, kDotMax + 1, 0, s>>>(partial, grid, kb, out1 + a0 * st1, st1,
                                                  out2 ? out2 + a0 * st2 : nullptr, st2, nrm ? norm2 : nullptr);
             SBD_LAUNCH("mdot_final");
@@ -471,13 +634,15 @@ struct Work {
     void axpys(const double *X, int64_t ldx, int k, const double *coef, double *y, double *norm2 = nullptr)
     {
         if (norm2) {
-            maxpy_kernel<true><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
+            if (pair) maxpy_kernel<true, true><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
+            else maxpy_kernel<true, false><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
             SBD_LAUNCH("maxpy_kernel");
             mdot_final<<<1, kDotMax + 1, 0, s>>>(partial, grid, 0, nullptr, 0, nullptr, 0, norm2);
             SBD_LAUNCH("mdot_final");
             globalize(norm2, 1, 1);
         } else {
-            maxpy_kernel<false><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
+            if (pair) maxpy_kernel<false, true><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
+            else maxpy_kernel<false, false><<<grid, kBlas, 0, s>>>(X, ldx, k, coef, y, N, partial);
             SBD_LAUNCH("maxpy_kernel");
         }
     }
@@ -518,12 +683,39 @@ struct Work {
                                   nullptr, 0.0, nullptr);
         }
     }
-    // the Ritz step: U, HU, the corrections tc and the residual norms (host) for j < m <= kRitzMax
-    void ritz(const double *V, const double *W, int64_t ld, int k, const double *Y, int ldy, int m, double *U,
+    // the Ritz step: U, HU, the corrections tc and the residual norms (host) for j < m <= kRitzMax.
+    // With one root, FP32 pairs, one process and k <= kDotMax, the same pass also leaves the first
+    // Gram-Schmidt projections V^T tc and tc . tc in partial2 (returns true; see proj_dots).
+    bool ritz(const double *V, const double *W, int64_t ld, int k, const double *Y, int ldy, int m, double *U,
               double *HU, const double *theta, const double *hd, double delta, double *tc, double *rn_host)
     {
-        launch_combine<true>(V, W, ld, k, Y, ldy, m, U, HU, ld, theta, hd, delta, tc);
+        const bool fuse = pair && m == 1 && k >= 1 && k <= kDotMax && (!sh || sh->world == 1) && partial2;
+        if (!fuse) {
+            launch_combine<true>(V, W, ld, k, Y, ldy, m, U, HU, ld, theta, hd, delta, tc);
+        } else {
+            if (k <= 8)
+                ritz_dots_kernel<8><<<grid, kBlas, ritz_dots_smem<8>(), s>>>(V, W, ld, k, Y, U, HU, theta, hd, delta,
+                                                                           tc, partial, partial2, N);
+            else if (k <= 16)
+                ritz_dots_kernel<16><<<grid, kBlas, ritz_dots_smem<16>(), s>>>(V, W, ld, k, Y, U, HU, theta, hd,
+                                                                             delta, tc, partial, partial2, N);
+            else if (k <= 24)
+                ritz_dots_kernel<24><<<grid, kBlas, ritz_dots_smem<24>(), s>>>(V, W, ld, k, Y, U, HU, theta, hd,
+                                                                             delta, tc, partial, partial2, N);
+            else
+                ritz_dots_kernel<kDotMax><<<grid, kBlas, ritz_dots_smem<kDotMax>(), s>>>(
+                    V, W, ld, k, Y, U, HU, theta, hd, delta, tc, partial, partial2, N);
+            SBD_LAUNCH("ritz_dots_kernel");
+        }
         reduce_norms(m, rn_host);
+        return fuse;
+    }
+    // coef[a] = X[a] . tc (a < k) and *norm2 = tc . tc from the sums the fused Ritz pass left in
+    // partial2; valid while X, k and tc are those of that pass
+    void proj_dots(int k, double *coef, double *norm2)
+    {
+        mdot_final<<<1, kDotMax + 1, 0, s>>>(partial2, grid, k, coef, 1, nullptr, 0, norm2);
+        SBD_LAUNCH("mdot_final");
     }
     void reduce_norms(int m, double *rn_host)
     {
@@ -673,6 +865,12 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
     r.status = SBD_OK;
     SBD_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(2 * sizeof(double) * kMaxSub * kMaxSub)));
+    SBD_CUDA(cudaFuncSetAttribute(ritz_dots_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  ritz_dots_smem<16>()));
+    SBD_CUDA(cudaFuncSetAttribute(ritz_dots_kernel<24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  ritz_dots_smem<24>()));
+    SBD_CUDA(cudaFuncSetAttribute(ritz_dots_kernel<kDotMax>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  ritz_dots_smem<kDotMax>()));
 
     Work w(c, N, off, shard);
     w.pair = prec == SBD_F32X2 || (mixed && exact_prec == SBD_F32X2);
@@ -698,6 +896,7 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
         double *dscr = (double *)grab(sizeof(double) * kMaxSub);
         int64_t *dexcl = (int64_t *)grab(sizeof(int64_t) * (kRitzMax + 1));
         w.partial = (double *)grab(sizeof(double) * (size_t)w.grid * kPart);
+        w.partial2 = (double *)grab(sizeof(double) * (size_t)w.grid * kPart);
         w.pv = (double *)grab(sizeof(double) * w.grid);
         w.pi = (int64_t *)grab(sizeof(int64_t) * w.grid);
         w.dscal = (double *)grab(sizeof(double) * (kMaxSub + 1));
@@ -779,7 +978,8 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
             jacobi_kernel<<<1, 256, 2 * sizeof(double) * k * k, w.s>>>(T, kMaxSub, k, theta, Y, kMaxSub);
             SBD_LAUNCH("jacobi_kernel");
             // 2d + 2f. Ritz vectors, residual norms and the preconditioned corrections in one pass
-            w.ritz(V, W, ld, k, Y, kMaxSub, nroots, U, HU, theta, hd, delta, TC, rn.data());
+            // proj_ok: V, k and TC still those of the fused pass (cleared by a refinement or a restart)
+            bool proj_ok = w.ritz(V, W, ld, k, Y, kMaxSub, nroots, U, HU, theta, hd, delta, TC, rn.data());
             SBD_CUDA(cudaMemcpyAsync(th.data(), theta, sizeof(double) * k, cudaMemcpyDeviceToHost, w.s));
             SBD_CUDA(cudaStreamSynchronize(w.s));
             k_ritz = k;
@@ -805,8 +1005,9 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
                     sigma_cols(0, nroots, true);
                     SBD_CUDA(cudaMemcpyAsync(HU, W, (size_t)nroots * N * sizeof(double), cudaMemcpyDeviceToDevice, w.s));
                     for (int j = 0; j < nroots; ++j) {
-                        w.dots(U + j * ld, 0, 1, HU + j * ld, dscr + 2 * j, 1);
-                        w.dots(U + j * ld, 0, 1, U + j * ld, dscr + 2 * j + 1, 1);
+                        // the Rayleigh quotients that decide convergence: FP64 products
+                        w.dots(U + j * ld, 0, 1, HU + j * ld, dscr + 2 * j, 1, nullptr, 0, nullptr, true);
+                        w.dots(U + j * ld, 0, 1, U + j * ld, dscr + 2 * j + 1, 1, nullptr, 0, nullptr, true);
                     }
                     std::vector<double> hd2(2 * nroots);
                     SBD_CUDA(cudaMemcpyAsync(hd2.data(), dscr, sizeof(double) * 2 * nroots, cudaMemcpyDeviceToHost, w.s));
@@ -822,6 +1023,7 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
                     rmax = *std::max_element(rn.begin(), rn.end());
                     r.refinements++;
                     checked = true;
+                    proj_ok = false;
                     if (c.opt.verbose)
                         fprintf(stderr, "[sbd] refine %d theta0=%.12f rmax(fp64)=%.3e k=%d\n", r.refinements,
                                 th[0] + c.opt.ecore, rmax, nk);
@@ -853,6 +1055,7 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
                 const int nk = std::min(nkeep, k);
                 compress(k, nk);
                 k = nk;
+                proj_ok = false;
                 if (mixed)
                     for (int a = 0; a < k; ++a) exact[a] = 0;
                 // V' = V Y, W' = W Y with orthonormal Y: the projected matrix is diag(theta)
@@ -869,7 +1072,8 @@ int davidson(Ctx &c, int nroots, double tol, sbd_precision prec, double *energie
             for (int j = 0; j < nroots; ++j) {
                 if (rn[j] <= tol) continue;
                 double *t = TC + j * ld;
-                w.dots(V, ld, k, t, coef, 1, nullptr, 0, dscr + 0);     // c = V^T t, |t|^2 before
+                if (proj_ok) w.proj_dots(k, coef, dscr + 0);           // from the Ritz pass
+                else w.dots(V, ld, k, t, coef, 1, nullptr, 0, dscr + 0); // c = V^T t, |t|^2 before
                 w.axpys(V, ld, k, coef, t, dscr + 1);                   // t -= V c, |t|^2 after
                 double nn[2];
                 SBD_CUDA(cudaMemcpyAsync(nn, dscr, sizeof(nn), cudaMemcpyDeviceToHost, w.s));

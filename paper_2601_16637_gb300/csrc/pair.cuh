@@ -16,23 +16,26 @@ struct F2 {
     __host__ __device__ constexpr F2(float h, float l) : hi(h), lo(l) {}
 };
 
-// x = hi + lo to 48 bits.  Done on the integer pipe: hi keeps the sign, the exponent and the top 23
-// mantissa bits of x (truncation), lo is the value of the 29 bits cut off; only |x| outside the FP32
-// normal range takes the FP64 route (FP64 conversions and subtraction run on the FP64 pipe, which on
-// this GPU is ~1/64 of the FP32 rate and would otherwise dominate the staging of pair amplitudes).
+// x = hi + lo to 48 bits, on the integer and FP32 pipes only, without branches.  hi keeps the sign,
+// the exponent and the top 23 mantissa bits of x (truncation); lo is the value of the 29 bits cut
+// off, converted to FP32 and scaled by two exact power-of-two products.  Outside the FP32 normal
+// range selects give: |x| < 2^-126 (zeros included) a signed zero, |x| >= 2^128 and infinities an
+// infinity, NaN a NaN.  (An FP64 fallback or a branch here costs every element: the compiler
+// if-converts the fallback, whose FP64 conversions run at ~1/64 of the FP32 rate on this GPU, and
+// the streaming kernels of the solver spend most of their instructions in this split.)
 __device__ __forceinline__ F2 f2_split(double x)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned int h = (unsigned int)(b >> 32), l = (unsigned int)b;
-    const int e = (int)((h >> 20) & 0x7FFu);  // biased FP64 exponent
-    if (e < 1023 - 126 || e > 1023 + 127) {
-        const float hi = __double2float_rn(x);
-        return F2(hi, __double2float_rn(x - (double)hi));
-    }
-    const unsigned int sign = h & 0x80000000u;
-    const float hi = __uint_as_float(sign | ((unsigned int)(e - 1023 + 127) << 23) | ((h & 0xFFFFFu) << 3) | (l >> 29));
-    const float lo = ldexpf(__uint2float_rn(l & 0x1FFFFFFFu), e - 1023 - 52);
-    return F2(hi, sign ? -lo : lo);
+    const unsigned int sign = h & 0x80000000u, ha = h ^ sign;  // ha: high word of |x|
+    const bool in = ha - 0x38100000u < 0x0FE00000u;             // biased FP64 exponent in [897, 1150]
+    // in range, ha - (896 << 20) holds the FP32 exponent (1..254) above the top 20 mantissa bits
+    const unsigned int t = (ha - 0x38000000u) << 3;
+    const float lo = __uint2float_rn(l & 0x1FFFFFFFu) * 0x1p-52f * __uint_as_float(t & 0x7F800000u);
+    const unsigned int big = sign | 0x7F800000u | ((ha | (unsigned int)(l != 0u)) > 0x7FF00000u ? 0x400000u : 0u);
+    const unsigned int hb = in ? (sign | t | (l >> 29)) : (ha >= 0x47F00000u ? big : sign);
+    const unsigned int lb = in ? (__float_as_uint(lo) ^ sign) : 0u;
+    return F2(__uint_as_float(hb), __uint_as_float(lb));
 }
 __device__ __forceinline__ double f2_value(F2 a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ F2 f2_neg(F2 a) { return F2(-a.hi, -a.lo); }

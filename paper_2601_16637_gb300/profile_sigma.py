@@ -5,6 +5,11 @@ normalised random vector and prints the per-kernel device times measured with
 CUDA events on the launch stream (sbd_kernel_times).  Holds only the tables,
 one vector, its transpose and sigma on the device, which keeps it suitable as
 the command a profiler captures.
+
+With `--solve`, runs one Davidson solve of the workload instead (its own
+precision, tolerance and subspace size), so that the solver's vector kernels
+can be captured; `--strings n` shrinks |A| = |B| to n to keep such a capture
+small.
 """
 from __future__ import annotations
 
@@ -19,6 +24,8 @@ def main() -> None:
     ap.add_argument("--workload", default="cfg3-6000")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "f32x2"])
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--solve", action="store_true", help="one Davidson solve instead of sigma products")
+    ap.add_argument("--strings", type=int, default=0, help="override |A| = |B|")
     args = ap.parse_args()
 
     import torch
@@ -27,7 +34,20 @@ def main() -> None:
     from . import workloads as W
 
     B.load(build_if_missing=True)
-    wl = W.config(args.workload)
+    over = {"nA": args.strings, "nB": args.strings} if args.strings > 0 else {}
+    wl = W.config(args.workload, **over)
+    if args.solve:
+        import time
+        with B.SBD.from_workload(wl, max_subspace=wl.max_subspace) as g:
+            t0 = time.perf_counter()
+            res = g.davidson(wl.nroots, wl.tol, wl.precision, vectors=None)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+        print(json.dumps({"workload": wl.name, "ndets": wl.ndets, "energies": [float(e) for e in res.energies],
+                          "status": res.status, "seconds": sec, "report": res.report}, default=str))
+        if res.status != 0:
+            raise SystemExit(1)
+        return
     g = B.SBD.from_workload(wl, timing=True)
     x = torch.from_numpy(W.random_vector(g.N, 100)[0]).cuda()
     if args.precision == "mixed":
