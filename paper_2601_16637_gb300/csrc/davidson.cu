@@ -77,7 +77,7 @@ __device__ __forceinline__ T block_sum(T v, T *red)
 // partial[b*kPart + a] = sum over block b's elements of X[a][i] y[i] (a < k <= kDotMax);
 // with NORM also partial[b*kPart + kDotMax] = sum y[i]^2
 template <bool NORM, int KB>
-__global__ void __launch_bounds__(kBlas) mdot_partial(const double *__restrict__ X, int64_t ldx, int k,
+__global__ void __launch_bounds__(kBlas, KB <= 16 ? 4 : 2) mdot_partial(const double *__restrict__ X, int64_t ldx, int k,
                                                       const double *__restrict__ y, int64_t N, double *partial)
 {
     __shared__ double red[kBlas / 32];
@@ -405,7 +405,7 @@ constexpr int ritz_dots_smem()
 }
 
 // partial[b*kPart + j] = sum over block b of (HU[j] - theta[j] U[j])^2, j < m <= kRitzMax
-__global__ void __launch_bounds__(kBlas) resid_partial(const double *__restrict__ U, const double *__restrict__ HU,
+__global__ void __launch_bounds__(kBlas, 4) resid_partial(const double *__restrict__ U, const double *__restrict__ HU,
                                                        int64_t ld, int m, const double *__restrict__ theta,
                                                        int64_t N, double *partial)
 {
@@ -692,39 +692,48 @@ struct Work {
         const bool fuse = pair && m == 1 && k >= 1 && k <= kDotMax && (!sh || sh->world == 1) && partial2;
         if (!fuse) {
             launch_combine<true>(V, W, ld, k, Y, ldy, m, U, HU, ld, theta, hd, delta, tc);
-        } else {
-            if (k <= 8)
-                ritz_dots_kernel<8><<<grid, kBlas, ritz_dots_smem<8>(), s>>>(V, W, ld, k, Y, U, HU, theta, hd, delta,
-                                                                           tc, partial, partial2, N);
-            else if (k <= 16)
-                ritz_dots_kernel<16><<<grid, kBlas, ritz_dots_smem<16>(), s>>>(V, W, ld, k, Y, U, HU, theta, hd,
-                                                                             delta, tc, partial, partial2, N);
-            else if (k <= 24)
-                ritz_dots_kernel<24><<<grid, kBlas, ritz_dots_smem<24>(), s>>>(V, W, ld, k, Y, U, HU, theta, hd,
-                                                                             delta, tc, partial, partial2, N);
-            else
-                ritz_dots_kernel<kDotMax><<<grid, kBlas, ritz_dots_smem<kDotMax>(), s>>>(
-                    V, W, ld, k, Y, U, HU, theta, hd, delta, tc, partial, partial2, N);
-            SBD_LAUNCH("ritz_dots_kernel");
+            reduce_norms(m, rn_host);
+            return false;
         }
-        reduce_norms(m, rn_host);
-        return fuse;
+        // every block of the fused pass resident at once: a grid-strided block left for a second
+        // wave would run its whole share at a fraction of the occupancy
+        if (k <= 8) launch_ritz_dots<8>(V, W, ld, k, Y, U, HU, theta, hd, delta, tc);
+        else if (k <= 16) launch_ritz_dots<16>(V, W, ld, k, Y, U, HU, theta, hd, delta, tc);
+        else if (k <= 24) launch_ritz_dots<24>(V, W, ld, k, Y, U, HU, theta, hd, delta, tc);
+        else launch_ritz_dots<kDotMax>(V, W, ld, k, Y, U, HU, theta, hd, delta, tc);
+        reduce_norms(m, rn_host, rgrid);
+        return true;
+    }
+    int rgrid = 0;  // blocks of the last fused Ritz pass (partial sums in partial, partial2)
+    template <int KB>
+    void launch_ritz_dots(const double *V, const double *W, int64_t ld, int k, const double *Y, double *U,
+                          double *HU, const double *theta, const double *hd, double delta, double *tc)
+    {
+        int per_sm = 0;
+        SBD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ritz_dots_kernel<KB>, kBlas,
+                                                               ritz_dots_smem<KB>()));
+        rgrid = std::max(1, std::min(grid, per_sm * (c.num_sms > 0 ? c.num_sms : 152)));
+        ritz_dots_kernel<KB><<<rgrid, kBlas, ritz_dots_smem<KB>(), s>>>(V, W, ld, k, Y, U, HU, theta, hd, delta, tc,
+                                                                         partial, partial2, N);
+        SBD_LAUNCH("ritz_dots_kernel");
     }
     // coef[a] = X[a] . tc (a < k) and *norm2 = tc . tc from the sums the fused Ritz pass left in
     // partial2; valid while X, k and tc are those of that pass
     void proj_dots(int k, double *coef, double *norm2)
     {
-        mdot_final<<<1, kDotMax + 1, 0, s>>>(partial2, grid, k, coef, 1, nullptr, 0, norm2);
+        mdot_final<<<1, kDotMax + 1, 0, s>>>(partial2, rgrid, k, coef, 1, nullptr, 0, norm2);
         SBD_LAUNCH("mdot_final");
     }
-    void reduce_norms(int m, double *rn_host)
+    // nb: blocks that wrote partial (0: the BLAS grid)
+    void reduce_norms(int m, double *rn_host, int nb = 0)
     {
-        hpart.assign((size_t)grid * kPart, 0.0);
-        SBD_CUDA(cudaMemcpyAsync(hpart.data(), partial, sizeof(double) * grid * kPart, cudaMemcpyDeviceToHost, s));
+        if (nb <= 0) nb = grid;
+        hpart.assign((size_t)nb * kPart, 0.0);
+        SBD_CUDA(cudaMemcpyAsync(hpart.data(), partial, sizeof(double) * nb * kPart, cudaMemcpyDeviceToHost, s));
         SBD_CUDA(cudaStreamSynchronize(s));
         std::vector<double> acc((size_t)m, 0.0);
         for (int j = 0; j < m; ++j)
-            for (int b = 0; b < grid; ++b) acc[j] += hpart[(size_t)b * kPart + j];
+            for (int b = 0; b < nb; ++b) acc[j] += hpart[(size_t)b * kPart + j];
         allreduce(acc.data(), m);
         for (int j = 0; j < m; ++j) rn_host[j] = sqrt(acc[j]);
     }
