@@ -86,7 +86,11 @@ struct SpinTables {
     int64_t half = 0;
     int64_t *hs_ptr = nullptr, *hd_ptr = nullptr;  // [2n + 1]
     uint2 *hs = nullptr;  // (packed single, FP32 value bits)
-    uint2 *hd = nullptr;  // (target, FP32 value bits)
+    // doubles as two arrays with the same entry index: FP32 values, and targets relative to the
+    // list's column half (0 for the lower half, `half` for the upper), which fit 16 bits: the split
+    // lists are built only for half <= 65536 (six bytes per entry instead of eight)
+    float *hdv = nullptr;
+    uint16_t *hdt = nullptr;
     // Source-major singles for the column-stationary alpha-beta pass.  The canonical singles list
     // of each string is cut into items of at most kSrcItem entries (strings in ascending order,
     // each string's items consecutive, then inside each slice of 32 items the full ones first and

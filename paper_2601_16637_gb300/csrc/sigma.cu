@@ -281,7 +281,9 @@ struct RowArgs {
     Lists<T> lists;
     // mixed passes over column halves (row_halves): the column spin's lists split at `half`
     const int64_t *hls_ptr, *hld_ptr;  // singles, doubles: [2n + 1]
-    const uint2 *hls, *hld;
+    const uint2 *hls;                  // (packed single, FP32 value bits)
+    const float *hldv;                 // doubles: FP32 values
+    const uint16_t *hldt;              // doubles: targets relative to their column half
     int64_t half;
 };
 
@@ -572,15 +574,15 @@ __device__ __forceinline__ void row_halves(const RowArgs<float> &a, int64_t r0, 
                     if (kListPad * lig >= lc) break;
                     int64_t e0, e1;
                     list_slots(d0, cb2, lc, lig, e0, e1);
-                    const uint4 p0 = __ldg(reinterpret_cast<const uint4 *>(a.hld + e0));
-                    const uint4 p1 = __ldg(reinterpret_cast<const uint4 *>(a.hld + e1));
-                    const uint32_t jj[4] = {p0.x, p0.z, p1.x, p1.z};
-                    const float vv[4] = {__uint_as_float(p0.y), __uint_as_float(p0.w), __uint_as_float(p1.y),
-                                         __uint_as_float(p1.w)};
+                    // entries e0 .. e0 + 3: four values (16 bytes) and four 16-bit targets (8 bytes)
+                    const float4 v4 = __ldg(reinterpret_cast<const float4 *>(a.hldv + e0));
+                    const uint2 t4 = __ldg(reinterpret_cast<const uint2 *>(a.hldt + e0));
+                    const uint32_t jj[4] = {t4.x & 0xFFFFu, t4.x >> 16, t4.y & 0xFFFFu, t4.y >> 16};
+                    const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        // padding entries have target 0 and value 0: point them at the staged row 0
-                        const int64_t jl = max((int64_t)jj[u] - c0, (int64_t)0);
+                        // targets are relative to the staged half; padding entries: target 0, value 0
+                        const int64_t jl = (int64_t)jj[u];
                         const float4 xa = *reinterpret_cast<const float4 *>(Xa + jl * 4);
                         const float4 xb = *reinterpret_cast<const float4 *>(Xb + jl * 4);
                         acc[0] += vv[u] * xa.x;
@@ -1275,7 +1277,8 @@ void make_args(const Ctx &c, const typename In<T>::type *C, double *S, const dou
     rb.hls_ptr = tb.hs_ptr;
     rb.hld_ptr = tb.hd_ptr;
     rb.hls = tb.hs;
-    rb.hld = tb.hd;
+    rb.hldv = tb.hdv;
+    rb.hldt = tb.hdt;
     rb.half = tb.half;
 
     ra = rb;
@@ -1295,7 +1298,8 @@ void make_args(const Ctx &c, const typename In<T>::type *C, double *S, const dou
     ra.hls_ptr = ta.hs_ptr;
     ra.hld_ptr = ta.hd_ptr;
     ra.hls = ta.hs;
-    ra.hld = ta.hd;
+    ra.hldv = ta.hdv;
+    ra.hldt = ta.hdt;
     ra.half = ta.half;
 
     ab = AbArgs<T>{};

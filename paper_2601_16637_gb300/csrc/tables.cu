@@ -536,6 +536,20 @@ __global__ void half_split_kernel(const int64_t *__restrict__ ptr, const int32_t
     }
 }
 
+// Doubles of the half-split lists: val[o] = FP32 of v[perm[o]], tgt[o] = its target relative to
+// the column half it lies in (target - half for targets >= half); zeros for padding
+__global__ void gather_half_doubles_kernel(const int64_t *__restrict__ perm, int64_t m,
+                                           const int32_t *__restrict__ j, const double *__restrict__ v,
+                                           int64_t half, float *val, uint16_t *tgt)
+{
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < m; o += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = perm[o];
+        const int64_t jj = e >= 0 ? (int64_t)j[e] : 0;
+        val[o] = e >= 0 ? __double2float_rn(v[e]) : 0.f;
+        tgt[o] = (uint16_t)(jj >= half ? jj - half : jj);
+    }
+}
+
 // out[o] = (key[perm[o]], FP32 of val[perm[o]]), zeros for padding
 __global__ void gather_pair_kernel(const int64_t *__restrict__ perm, int64_t m, const uint32_t *__restrict__ key,
                                    const double *__restrict__ val, uint2 *out)
@@ -774,8 +788,9 @@ void build_tables(Ctx &c, int spin)
         SBD_LAUNCH("split_kernel(doubles)");
     }
     dfree(c, perm);
-    // mixed-sigma lists split at the middle of the set (row passes over column halves)
-    {
+    // mixed-sigma lists split at the middle of the set (row passes over column halves); their
+    // 16-bit doubles targets need half <= 65536 (the staged halves fit shared memory only far below)
+    if ((n + 1) / 2 <= 65536) {
         t.half = (n + 1) / 2;
         int64_t *ptr2 = dalloc_n<int64_t>(c, 2 * (size_t)n + 1);
         int64_t *cnt2 = dalloc_n<int64_t>(c, 2 * (size_t)n);
@@ -783,7 +798,6 @@ void build_tables(Ctx &c, int spin)
             const int64_t *ptr = kind == 0 ? t.s_ptr : t.d_ptr;
             const int32_t *tgt = kind == 0 ? t.s_j : t.d_j;
             int64_t *&hptr = kind == 0 ? t.hs_ptr : t.hd_ptr;
-            uint2 *&hout = kind == 0 ? t.hs : t.hd;
             half_split_kernel<<<blocks_for(n, 256), 256, 0, c.stream>>>(ptr, tgt, n, t.half, ptr2);
             SBD_LAUNCH("half_split_kernel");
             hptr = dalloc_n<int64_t>(c, 2 * (size_t)n + 1);
@@ -794,16 +808,27 @@ void build_tables(Ctx &c, int spin)
             int64_t m = 0;
             SBD_CUDA(cudaMemcpyAsync(&m, hptr + 2 * n, sizeof(int64_t), cudaMemcpyDeviceToHost, c.stream));
             SBD_CUDA(cudaStreamSynchronize(c.stream));
-            hout = dalloc_n<uint2>(c, (size_t)std::max<int64_t>(m, 1));
+            const size_t mm = (size_t)std::max<int64_t>(m, 1);
+            if (kind == 0) {
+                t.hs = dalloc_n<uint2>(c, mm);
+            } else {
+                t.hdv = dalloc_n<float>(c, mm);
+                t.hdt = dalloc_n<uint16_t>(c, mm);
+            }
             if (m) {
                 int64_t *hperm = dalloc_n<int64_t>(c, (size_t)m);
                 sigma_order_kernel<<<blocks_for(2 * n, 128), 128, 0, c.stream>>>(ptr2, hptr, 2 * n, tgt,
                                                                                   kind == 0 ? t.s_pk : nullptr, hperm);
                 SBD_LAUNCH("sigma_order_kernel(halves)");
-                gather_pair_kernel<<<blocks_for(m, 256, 16384), 256, 0, c.stream>>>(
-                    hperm, m, kind == 0 ? t.s_pk : reinterpret_cast<const uint32_t *>(t.d_j),
-                    kind == 0 ? t.s_v64 : t.d_v64, hout);
-                SBD_LAUNCH("gather_pair_kernel(halves)");
+                if (kind == 0) {
+                    gather_pair_kernel<<<blocks_for(m, 256, 16384), 256, 0, c.stream>>>(hperm, m, t.s_pk, t.s_v64,
+                                                                                         t.hs);
+                    SBD_LAUNCH("gather_pair_kernel(halves)");
+                } else {
+                    gather_half_doubles_kernel<<<blocks_for(m, 256, 16384), 256, 0, c.stream>>>(
+                        hperm, m, t.d_j, t.d_v64, t.half, t.hdv, t.hdt);
+                    SBD_LAUNCH("gather_half_doubles_kernel");
+                }
                 dfree(c, hperm);
             }
         }
