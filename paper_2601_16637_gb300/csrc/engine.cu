@@ -24,6 +24,12 @@
 // pinned memory (copied by the graph's first node), replays, and reads back a
 // small status array.  All per-slot decisions (converged, restart, check) are
 // taken on the host between the two graphs.
+//
+// The vector operations of the Davidson steps (Ritz combinations, Gram-Schmidt
+// dot products and updates, the projected-matrix column, the restart) sum in
+// FP32 pairs (pair.cuh: 48-bit operands on the FP32 pipe; GB300's FP64 pipe
+// runs one multiply-add per loaded element below the HBM rate); the FP64 check
+// of a converged vector (its Rayleigh quotient and residual) stays FP64.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -34,10 +40,12 @@
 #include <map>
 #include <memory>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
 #include "jacobi.cuh"
+#include "pair.cuh"
 
 namespace sbd {
 
@@ -126,7 +134,7 @@ __global__ void __launch_bounds__(kEThreads) e_ritz_kernel(const Header *hdr, co
                                                           const int *chunk_slot, const int64_t *chunk_off,
                                                           double *partial)
 {
-    __shared__ double ys[kEMaxSub];
+    __shared__ F2 ys[kEMaxSub];
     __shared__ double red[kEThreads / 32];
     const int nchunk = hdr->nchunk;
     for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
@@ -135,13 +143,13 @@ __global__ void __launch_bounds__(kEThreads) e_ritz_kernel(const Header *hdr, co
         if (!(d.kind & kRitz)) continue;
         const int k = d.k;
         __syncthreads();
-        for (int a = threadIdx.x; a < k; a += kEThreads) ys[a] = d.Y[a * kEMaxSub];
+        for (int a = threadIdx.x; a < kEMaxSub; a += kEThreads) ys[a] = a < k ? f2_split(d.Y[a * kEMaxSub]) : F2(0.f);
         __syncthreads();
         const double th = d.theta[0], delta = d.delta;
         const int64_t e0 = chunk_off[c], e1 = min(e0 + kChunk, d.N);
         double racc = 0.0;
         for (int64_t i = e0 + threadIdx.x; i < e1; i += kEThreads) {
-            double u = 0.0, hu = 0.0;
+            F2 up(0.f), hup(0.f);
             for (int a0 = 0; a0 < k; a0 += kLoadE) {
                 double x[kLoadE], h[kLoadE];
 #pragma unroll
@@ -151,12 +159,13 @@ __global__ void __launch_bounds__(kEThreads) e_ritz_kernel(const Header *hdr, co
                     h[q] = ok ? d.W[(a0 + q) * d.N + i] : 0.0;
                 }
 #pragma unroll
-                for (int q = 0; q < kLoadE; ++q) {
-                    const double y = a0 + q < k ? ys[a0 + q] : 0.0;
-                    u += y * x[q];
-                    hu += y * h[q];
-                }
+                for (int q = 0; q < kLoadE; ++q)
+                    if (a0 + q < k) {
+                        f2_mac(up, ys[a0 + q], f2_split(x[q]));
+                        f2_mac(hup, ys[a0 + q], f2_split(h[q]));
+                    }
             }
+            const double u = f2_value(up), hu = f2_value(hup);
             const double r = hu - th * u;
             racc += r * r;
             const double dd = d.hd[i] - th;
@@ -195,9 +204,11 @@ __global__ void __launch_bounds__(kEThreads) e_dots_kernel(const Header *hdr, co
         const int64_t e0 = chunk_off[c], e1 = min(e0 + kChunk, d.N);
         // sweeps of G vectors (the norm rides on the first sweep); at least one sweep for the norm
         for (int a0 = 0; a0 < cnt || (a0 == 0 && NORM); a0 += G) {
-            double acc[G];
+            // MODE 0, 1: pair products; MODE 2 (the FP64 check): FP64
+            using Acc = typename std::conditional<MODE == 2, double, F2>::type;
+            Acc acc[G];
 #pragma unroll
-            for (int q = 0; q < G; ++q) acc[q] = 0.0;
+            for (int q = 0; q < G; ++q) acc[q] = Acc(0.f);
             double nacc = 0.0;
             for (int64_t i = e0 + threadIdx.x; i < e1; i += kEThreads) {
                 double x[G];
@@ -208,13 +219,22 @@ __global__ void __launch_bounds__(kEThreads) e_dots_kernel(const Header *hdr, co
                     const double zi = z[i];
                     nacc += zi * zi;
                 }
+                if constexpr (MODE == 2) {
 #pragma unroll
-                for (int q = 0; q < G; ++q) acc[q] += x[q] * yi;
+                    for (int q = 0; q < G; ++q) acc[q] += x[q] * yi;
+                } else {
+                    const F2 ys = f2_split(yi);
+#pragma unroll
+                    for (int q = 0; q < G; ++q) f2_mac(acc[q], f2_split(x[q]), ys);
+                }
             }
 #pragma unroll
             for (int q = 0; q < G; ++q)
                 if (a0 + q < cnt) {
-                    const double sum = block_sum(acc[q], red);
+                    double v;
+                    if constexpr (MODE == 2) v = acc[q];
+                    else v = f2_value(acc[q]);
+                    const double sum = block_sum(v, red);
                     if (threadIdx.x == 0) partial[(int64_t)c * kEPart + a0 + q] = sum;
                 }
             if (NORM && a0 == 0) {
@@ -232,7 +252,7 @@ __global__ void __launch_bounds__(kEThreads) e_axpy_kernel(const Header *hdr, co
                                                           const int *chunk_slot, const int64_t *chunk_off,
                                                           double *partial)
 {
-    __shared__ double cs[kEMaxSub];
+    __shared__ F2 cs[kEMaxSub];
     __shared__ double red[kEThreads / 32];
     const int nchunk = hdr->nchunk;
     for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
@@ -241,20 +261,21 @@ __global__ void __launch_bounds__(kEThreads) e_axpy_kernel(const Header *hdr, co
         if (SECOND && d.red[kRedNeed2] == 0.0) continue;
         const int ke = keff(d);
         __syncthreads();
-        for (int a = threadIdx.x; a < ke; a += kEThreads) cs[a] = d.coef[a];
+        for (int a = threadIdx.x; a < ke; a += kEThreads) cs[a] = f2_split(d.coef[a]);
         __syncthreads();
         const int64_t e0 = chunk_off[c], e1 = min(e0 + kChunk, d.N);
         double nacc = 0.0;
         for (int64_t i = e0 + threadIdx.x; i < e1; i += kEThreads) {
-            double t = d.TC[i];
+            F2 sp(0.f);  // sum_a coef[a] V[a] in pairs, subtracted in FP64
             for (int a0 = 0; a0 < ke; a0 += kLoadE) {
                 double x[kLoadE];
 #pragma unroll
                 for (int q = 0; q < kLoadE; ++q) x[q] = a0 + q < ke ? d.V[(int64_t)(a0 + q) * d.N + i] : 0.0;
 #pragma unroll
                 for (int q = 0; q < kLoadE; ++q)
-                    if (a0 + q < ke) t -= cs[a0 + q] * x[q];
+                    if (a0 + q < ke) f2_mac(sp, cs[a0 + q], f2_split(x[q]));
             }
+            const double t = d.TC[i] - f2_value(sp);
             d.TC[i] = t;
             if (NORM) nacc += t * t;
         }
@@ -343,29 +364,29 @@ __global__ void e_final_kernel(const Header *hdr, SlotDev *slots, const double *
 __global__ void __launch_bounds__(kEThreads) e_compress_kernel(const Header *hdr, const SlotDev *slots,
                                                               const int *chunk_slot, const int64_t *chunk_off)
 {
-    __shared__ double ys[kEMaxSub * kEMaxSub];
+    __shared__ F2 ys[kEMaxSub * kEMaxSub];
     const int nchunk = hdr->nchunk;
     for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
         const SlotDev &d = slots[chunk_slot[c]];
         if (!(d.kind & kRestart)) continue;
         const int k = d.k, nk = d.nk;
         __syncthreads();
-        for (int t = threadIdx.x; t < k * nk; t += kEThreads) ys[t] = d.Y[(t / nk) * kEMaxSub + (t % nk)];
+        for (int t = threadIdx.x; t < k * nk; t += kEThreads) ys[t] = f2_split(d.Y[(t / nk) * kEMaxSub + (t % nk)]);
         __syncthreads();
         const int64_t e0 = chunk_off[c], e1 = min(e0 + kChunk, d.N);
         for (int64_t i = e0 + threadIdx.x; i < e1; i += kEThreads) {
 #pragma unroll 1
             for (int m = 0; m < 2; ++m) {
                 double *X = m == 0 ? d.V : d.W;
-                double x[kEMaxSub];
+                F2 x[kEMaxSub];
 #pragma unroll
-                for (int a = 0; a < kEMaxSub; ++a) x[a] = a < k ? X[(int64_t)a * d.N + i] : 0.0;
+                for (int a = 0; a < kEMaxSub; ++a) x[a] = a < k ? f2_split(X[(int64_t)a * d.N + i]) : F2(0.f);
                 for (int j = 0; j < nk; ++j) {
-                    double v = 0.0;
+                    F2 v(0.f);
 #pragma unroll
                     for (int a = 0; a < kEMaxSub; ++a)
-                        if (a < k) v += ys[a * nk + j] * x[a];
-                    X[(int64_t)j * d.N + i] = v;
+                        if (a < k) f2_mac(v, ys[a * nk + j], x[a]);
+                    X[(int64_t)j * d.N + i] = f2_value(v);
                 }
             }
         }

@@ -390,6 +390,24 @@ def test_davidson_restart_size_option(torch, B, med_pair, med_lanczos):
         assert res.status == 0 and np.abs(res.energies - e_ref).max() <= EIG_FP64_ATOL
 
 
+@pytest.mark.parametrize("prec,max_sub", [("f32x2", 32), ("mixed", 32), ("f32x2", 48), ("mixed", 12)])
+def test_davidson_one_root_basis_sizes(torch, B, med_pair, med_lanczos, prec, max_sub):
+    # one root in FP32 pairs: the Ritz pass also forms the Gram-Schmidt projections (basis of up to
+    # 32 vectors), larger bases take the separate projection pass; the pair dot products run in
+    # chunks of 8 basis vectors.  Every size must reach the Lanczos root and an FP64-accurate vector.
+    wl, g, o = med_pair
+    e_ref, v_ref = med_lanczos
+    with B.SBD.from_workload(wl, max_subspace=max_sub) as gs:
+        res = gs.davidson(nroots=1, tol=1e-8, precision=prec)
+        assert res.status == 0, res.report
+        assert abs(res.energies[0] - e_ref[0]) <= EIG_FP64_ATOL
+        u = res.vectors[0].cpu().numpy()
+        assert abs(np.linalg.norm(u) - 1) <= 1e-10
+        assert abs(abs(u @ v_ref[0]) - 1) <= 1e-8
+        r = o.sigma(u[None, :])[0] - res.energies[0] * u
+        assert np.linalg.norm(r) <= 1e-7
+
+
 def test_davidson_mixed_three_roots(torch, B, med_pair, med_lanczos):
     wl, g, o = med_pair
     e_ref, _ = med_lanczos
