@@ -92,7 +92,7 @@ typedef struct {
     double tol_energy;       /* > 0: a root also needs |theta_k - theta_(k-1)| <= tol_energy between
                                 consecutive iterations to count as converged (default 0: off) */
     int refine_precision;    /* FP64-accurate arithmetic of SBD_MIXED solves: SBD_F32X2 (default; the
-                                defect-correction sigma and the Ritz-vector combinations in FP32
+                                defect-correction sigma and the basis-vector arithmetic in FP32
                                 pairs) or SBD_FP64 (both on the FP64 pipe) */
     int restart_keep;        /* Ritz vectors a thick restart keeps; 0 = max(nroots, min(max_subspace -
                                 nroots, max(2 nroots, max_subspace/3))) */
@@ -210,8 +210,11 @@ int sbd_sigma(sbd_handle handle, const void *c_dev, double *sigma_dev, int nvec,
  *               with FP64-accurate defect correction (sbd_options.refine_precision;
  *               the converged residual is always FP64-accurate).  Vectors, the projected
  *               eigenproblem, residuals and energies stay FP64; with SBD_F32X2 (the whole
- *               solve, or refine_precision of a mixed one) the Ritz-vector combinations sum
- *               in FP32 pairs (48-bit products, one FP64 rounding per stored value)
+ *               solve, or refine_precision of a mixed one) the Ritz-vector combinations,
+ *               the Gram-Schmidt dot products and updates and the projected-matrix dot
+ *               products sum in FP32 pairs (48-bit products, one FP64 rounding per stored
+ *               value or per block sum); the Rayleigh quotients that decide convergence
+ *               after a defect correction are FP64 dot products
  *   energies_host  nroots doubles (ascending), ecore included
  *   vecs        NULL, or host or device pointer for [nroots][nA*nB] doubles
  *   residuals_host NULL or nroots doubles
@@ -356,7 +359,9 @@ int sbd_davidson_sharded(sbd_handle handle, const int64_t *bounds, const sbd_com
  * change of the Ritz value since the previous iteration is <= tol_energy; the
  * result is then checked with one FP64 sigma of the Ritz vector, whose FP64
  * residual must also be <= tol (else the job iterates on with a halved mixed
- * threshold).  Reported energy = FP64 Rayleigh quotient + ecore.
+ * threshold).  Reported energy = FP64 Rayleigh quotient + ecore.  The basis
+ * vector arithmetic (Ritz combinations, Gram-Schmidt, projected matrix, restart)
+ * sums in FP32 pairs (48-bit products); the check is FP64.
  * Orthogonalisation: classical Gram-Schmidt with a second pass when the first removed more than
  * half of the squared norm (the DGKS criterion, decided per job on the device); thick restart
  * to nkeep = max(2, max_subspace/3) Ritz vectors.
