@@ -172,6 +172,30 @@ def _mixed(torch, g, x):
     return g.sigma(torch.from_numpy(np.asarray(x)).float().cuda(), "mixed").cpu().numpy()
 
 
+def test_sigma_pair_split_edge_values(torch, B, med_pair):
+    # the FP32-pair sigma splits every amplitude into hi + lo on the integer pipe: exact zeros,
+    # magnitudes below the FP32 normal range (flushed to signed zeros: at most 2^-126 each) and
+    # large ones must give the FP64 sigma to FP64 accuracy; NaN amplitudes must give NaN
+    wl, g, o = med_pair
+    x = W.random_vector(g.N, 21)[0]
+    rng = np.random.default_rng(4)
+    idx = rng.permutation(g.N)
+    x[idx[:5000]] = 0.0
+    x[idx[5000:5100]] *= 1e-300
+    x[idx[5100:5200]] = np.copysign(1e-40, x[idx[5100:5200]])
+    x[idx[5200:5300]] *= 1e30
+    s64 = g.sigma(torch.from_numpy(x).cuda(), "fp64").cpu().numpy()
+    s2 = g.sigma(torch.from_numpy(x).cuda(), "f32x2").cpu().numpy()
+    assert rel_maxnorm(s2, s64) <= SIGMA_FP64_RTOL
+    # a vector of small values only (pair parts and cross products stay FP32-normal): same accuracy
+    y = W.random_vector(g.N, 22)[0] * 1e-20
+    assert rel_maxnorm(g.sigma(torch.from_numpy(y).cuda(), "f32x2").cpu().numpy(),
+                       g.sigma(torch.from_numpy(y).cuda(), "fp64").cpu().numpy()) <= SIGMA_FP64_RTOL
+    z = W.random_vector(g.N, 23)[0]
+    z[idx[7]] = np.nan
+    assert np.isnan(g.sigma(torch.from_numpy(z).cuda(), "f32x2").cpu().numpy()[idx[7]])
+
+
 def test_sigma_mixed_against_fp64(torch, B, med_pair):
     wl, g, o = med_pair
     x = W.random_vector(g.N, 9)[0]
