@@ -349,14 +349,14 @@ def engine_line(args, metric_value, elapsed, n_jobs, stats, extra, clk, config):
             "graph_launches": int(stats["graph_launches"]), "engine": stats, "clocks": clk, **extra}
 
 
-def batch_measure(B, insts, subspace: int, warmup: int, steps: int) -> dict:
+def batch_measure(B, insts, subspace: int, warmup: int, steps: int, schedule: str = "fair") -> dict:
     """One engine run over `insts` (persistent launches, CUDA graphs), `steps` times after `warmup`
     untimed runs on the two smallest instances, against the serial FP64 per-instance path on the
     same instances and stopping rule.  solves/s count converged jobs only (status 0)."""
     import torch
 
     opts = dict(max_slots=len(insts), max_subspace=subspace, max_norb=max(w.norb for w in insts),
-                max_strings=max(max(w.A.size, w.B.size) for w in insts), max_iter=400)
+                max_strings=max(max(w.A.size, w.B.size) for w in insts), max_iter=400, schedule=schedule)
     small = sorted(insts, key=lambda w: w.ndets)[:2]
     for _ in range(warmup):
         with B.Engine(**opts) as e:
@@ -394,7 +394,7 @@ def batch_measure(B, insts, subspace: int, warmup: int, steps: int) -> dict:
                         "status_counts": {str(k): sum(1 for r in results if r["status"] == k)
                                           for k in sorted({r["status"] for r in results})},
                         "iterations_min_median_max": [int(np.min(its)), float(np.median(its)), int(np.max(its))],
-                        "max_subspace": subspace, "rows_per_item": stats["rows_per_item"]},
+                        "max_subspace": subspace, "rows_per_item": stats["rows_per_item"], "schedule": schedule},
             "vs_serial_fp64": {"seconds": serial_t, "converged": conv64, "solves_per_s": conv64 / serial_t,
                                "iterations_min_median_max": [int(np.min(serial_it)), float(np.median(serial_it)),
                                                              int(np.max(serial_it))],
@@ -412,7 +412,7 @@ def run_batch(args):
     insts = W.batch_instances(args.batch_n)
     clocks = ClockSampler(0)
     clocks.start()
-    m = batch_measure(B, insts, args.engine_subspace, args.warmup, args.steps)
+    m = batch_measure(B, insts, args.engine_subspace, args.warmup, args.steps, args.engine_schedule)
     clk = clocks.stop()
     extra = {"batch": m["summary"], "vs_serial_fp64": m["vs_serial_fp64"]}
     config = {"workload": f"batch{len(insts)}: {len(insts)} instances, norb in {{16,20,24,26}}, "
@@ -449,14 +449,16 @@ def serve_once(B, opts, jobs):
         return results, base, e.stats()
 
 
-def serve_measure(B, built, traces, rates, subspace: int, budget_bytes: int, max_strings: int, warmup: int) -> dict:
+def serve_measure(B, built, traces, rates, subspace: int, budget_bytes: int, max_strings: int, warmup: int,
+                  schedule: str = "fair") -> dict:
     """Serves the jobs `built` (arrival times traces[rate]) with one engine per rate (continuous
     batching under a memory budget), and a FIFO queue served one job at a time by the serial FP64
     path on the same arrivals (measured service time per job).  Latencies count from arrival."""
     import torch
 
+    scheds = [x for x in str(schedule).split(",") if x]  # engine runs per schedule, one serial baseline
     opts = dict(max_slots=64, max_subspace=subspace, max_norb=max(w.norb for w in built), max_strings=max_strings,
-                max_iter=400, hbm_budget_bytes=int(budget_bytes))
+                max_iter=400, hbm_budget_bytes=int(budget_bytes), schedule=scheds[0])
     small = sorted(built, key=lambda w: w.ndets)[:2]
     for _ in range(warmup):
         with B.Engine(**opts) as e:
@@ -465,12 +467,13 @@ def serve_measure(B, built, traces, rates, subspace: int, budget_bytes: int, max
             e.run()
     torch.cuda.synchronize()
     runs = []
-    for r in rates:
-        jobs = [(t, w) for (t, _, _), w in zip(traces[r], built)]
-        results, base, stats = serve_once(B, opts, jobs)
-        arrivals = np.array([t for t, _ in jobs])
-        done = np.array([x["t_done"] - base for x in results])
-        runs.append((r, arrivals, done, results, stats))
+    for sc in scheds:
+        for r in rates:
+            jobs = [(t, w) for (t, _, _), w in zip(traces[r], built)]
+            results, base, stats = serve_once(B, {**opts, "schedule": sc}, jobs)
+            arrivals = np.array([t for t, _ in jobs])
+            done = np.array([x["t_done"] - base for x in results])
+            runs.append((r, arrivals, done, results, stats, sc))
     stream = torch.cuda.current_stream()
     service, dE, st64 = [], 0.0, []
     for w, res in zip(built, runs[0][3]):
@@ -481,7 +484,7 @@ def serve_measure(B, built, traces, rates, subspace: int, budget_bytes: int, max
             dE = max(dE, abs(e64 - res["energy"]))
     sweep = []
     n = len(built)
-    for r, arrivals, done, results, stats in runs:
+    for r, arrivals, done, results, stats, sc in runs:
         lat = done - arrivals
         span = float(done.max() - arrivals.min())
         conv = sum(1 for x in results if x["status"] == 0)
@@ -492,14 +495,15 @@ def serve_measure(B, built, traces, rates, subspace: int, budget_bytes: int, max
         lat64 = np.array(fin) - arrivals
         span64 = float(fin[-1] - arrivals.min())
         conv64 = sum(1 for x in st64 if x == 0)
-        sweep.append({"rate_per_s": r, "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+        sweep.append({"rate_per_s": r, "schedule": sc, "p50_s": float(np.percentile(lat, 50)),
+                      "p99_s": float(np.percentile(lat, 99)),
                       "makespan_s": span, "converged": conv, "solves_per_s": conv / span,
                       "bytes_peak": stats["bytes_peak"], "requeued": stats.get("requeued", 0),
                       "status_counts": {str(k): sum(1 for x in results if x["status"] == k)
                                         for k in sorted({x["status"] for x in results})},
                       "serial_fp64": {"p50_s": float(np.percentile(lat64, 50)), "p99_s": float(np.percentile(lat64, 99)),
                                       "makespan_s": span64, "converged": conv64, "solves_per_s": conv64 / span64}})
-    r0, arrivals, done, results, stats = runs[0]
+    r0, arrivals, done, results, stats, _ = runs[0]
     span = float(done.max() - arrivals.min())
     dets_sigma = sum(x["ndets"] * (x["sigma_mixed"] + x["sigma_fp64"]) for x in results)
     return {"span": span, "dets_sigma": dets_sigma, "stats": stats, "n": n,
@@ -508,7 +512,7 @@ def serve_measure(B, built, traces, rates, subspace: int, budget_bytes: int, max
                         "solves_per_s": sweep[0]["solves_per_s"], "status_counts": sweep[0]["status_counts"],
                         "bytes_peak": stats["bytes_peak"], "budget_bytes": opts["hbm_budget_bytes"],
                         "largest_job_dets": int(max(w.ndets for w in built)),
-                        "largest_norb": int(max(w.norb for w in built)), "sweep": sweep},
+                        "largest_norb": int(max(w.norb for w in built)), "schedule": scheds[0], "sweep": sweep},
             "vs_serial_fp64": {**sweep[0]["serial_fp64"], "service_s_total": float(sum(service)),
                                "max_abs_dE_Ha": dE, "statuses": {str(k): st64.count(k) for k in sorted(set(st64))}}}
 
@@ -542,7 +546,7 @@ def run_serve(args):
     clocks = ClockSampler(0)
     clocks.start()
     m = serve_measure(B, built, traces, rates, args.engine_subspace, int(args.budget_gb * 1e9),
-                      max(args.max_strings, 15000 if args.serve_big else 0), args.warmup)
+                      max(args.max_strings, 15000 if args.serve_big else 0), args.warmup, args.engine_schedule)
     clk = clocks.stop()
     m["serving"]["job_build_s"] = t_build
     extra = {"serving": m["serving"], "vs_serial_fp64": m["vs_serial_fp64"]}
@@ -673,6 +677,9 @@ def main():
     ap.add_argument("--max-strings", type=int, default=5000, help="largest |A| = |B| of the serve workload")
     ap.add_argument("--budget-gb", type=float, default=160.0, help="engine admission budget of the serve workload")
     ap.add_argument("--engine-subspace", type=int, default=20, help="Davidson basis per job in the engine")
+    ap.add_argument("--engine-schedule", default="fair",
+                    help="engine iterations: jobs share the device by cost (fair) or all jobs every iteration "
+                         "(lockstep); the serve workload takes a comma-separated list (one engine run each)")
     ap.add_argument("--serve-big", type=int, default=0,
                     help="serve workload: the last N jobs at norb 58, |A|=|B|=15,000 (the top of its range)")
     ap.add_argument("--legs", default="batch,serve",
@@ -682,6 +689,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    scheds = [x for x in args.engine_schedule.split(",") if x]
+    if not scheds or any(x not in ("fair", "lockstep") for x in scheds) or (len(scheds) > 1 and args.workload != "serve"):
+        ap.error("--engine-schedule: fair or lockstep (a comma-separated list only for --workload serve)")
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch64":
@@ -904,7 +914,7 @@ def main():
         want = {x.strip() for x in args.legs.split(",") if x.strip()}
         if "batch" in want:
             insts = W.batch_instances(64)[: args.leg_batch_n]
-            m = batch_measure(B, insts, args.engine_subspace, warmup=1, steps=1)
+            m = batch_measure(B, insts, args.engine_subspace, warmup=1, steps=1, schedule=args.engine_schedule)
             legs["batch"] = {"workload": f"the first {len(insts)} of the 64 batched instances (norb in "
                                          f"{{16,20,24,26}}, |A|,|B| in [500,5000])",
                              "engine_mixed": m["summary"], "serial_fp64": m["vs_serial_fp64"],
@@ -912,7 +922,7 @@ def main():
         if "serve" in want:
             traces, built, _ = serve_jobs(args.leg_requests, [args.rate], 5000)
             m = serve_measure(B, built, traces, [args.rate], args.engine_subspace, int(args.budget_gb * 1e9), 5000,
-                              warmup=1)
+                              warmup=1, schedule=args.engine_schedule)
             legs["serve"] = {"workload": f"{args.leg_requests} Poisson arrivals at {args.rate:g}/s, norb in "
                                          f"{{24,32,40,48,58}}, |A|=|B| log-uniform in [300,5000], "
                                          f"{args.budget_gb:g} GB budget",

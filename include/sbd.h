@@ -387,7 +387,18 @@ typedef struct {
      * head of the queue until running jobs free memory (or fails with SBD_ERR_OVER_BUDGET when no
      * other job holds memory). */
     size_t table_bytes_per_string;
+    /* Which jobs take part in an iteration.  SBD_SCHED_FAIR (default): jobs share the device by
+     * cost, stride scheduling on N = nA*nB: every job has a pass value that grows by N each
+     * iteration it takes part in, and an iteration runs the jobs whose pass is below the smallest
+     * pass plus the smallest N of the running jobs, so a job N times larger than the smallest
+     * iterates about once per N/N_min iterations while smaller ones run (equal device time per
+     * job; a job admitted later starts at the smallest pass).  SBD_SCHED_LOCKSTEP: every job
+     * takes part in every iteration.  The schedule changes when a job finishes, never what it
+     * computes. */
+    int schedule;
 } sbd_engine_options;
+
+enum { SBD_SCHED_FAIR = 0, SBD_SCHED_LOCKSTEP = 1 };
 
 typedef struct {
     int status;          /* SBD_OK, SBD_NOT_CONVERGED, or an error (< 0) */

@@ -59,7 +59,10 @@ class sbd_engine_options(C.Structure):
     _fields_ = [("max_slots", C.c_int), ("max_subspace", C.c_int), ("max_iter", C.c_int),
                 ("max_norb", C.c_int), ("max_strings", C.c_int), ("rows_per_item", C.c_int),
                 ("delta", C.c_double), ("hbm_budget_bytes", C.c_size_t), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", C.c_void_p), ("table_bytes_per_string", C.c_size_t)]
+                ("alloc_ctx", C.c_void_p), ("table_bytes_per_string", C.c_size_t), ("schedule", C.c_int)]
+
+
+SCHEDULE = {"fair": 0, "lockstep": 1}
 
 
 class sbd_job_result(C.Structure):
@@ -588,13 +591,16 @@ class Engine:
 
     def __init__(self, *, max_slots=64, max_subspace=12, max_iter=200, max_norb=64, max_strings=20000,
                  rows_per_item=0, delta=1e-4, hbm_budget_bytes=0, table_bytes_per_string=None,
-                 allocator: str = "torch", stream=None):
+                 schedule: str = "fair", allocator: str = "torch", stream=None):
         o = sbd_engine_default_options()
         o.max_slots, o.max_subspace, o.max_iter = max_slots, max_subspace, max_iter
         o.max_norb, o.max_strings, o.rows_per_item = max_norb, max_strings, rows_per_item
         o.delta, o.hbm_budget_bytes = delta, hbm_budget_bytes
         if table_bytes_per_string is not None:
             o.table_bytes_per_string = table_bytes_per_string
+        if schedule not in SCHEDULE:
+            raise ValueError("schedule must be 'fair' or 'lockstep'")
+        o.schedule = SCHEDULE[schedule]
         self._alloc = None
         if allocator == "torch":
             self._alloc = _TorchAllocator()

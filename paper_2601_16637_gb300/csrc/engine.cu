@@ -579,6 +579,8 @@ struct Slot {
     double theta_prev = NAN, thr = 0.0, r_mixed = INFINITY;
     std::vector<double> hist;  // mixed residuals since the last FP64 check
     int64_t chunk0 = 0, chunk1 = 0;
+    double pass = 0.0;      // fair schedule: device work taken so far, in determinants per iteration
+    bool run = false;       // takes part in the current iteration
 };
 
 struct sbd_engine_s {
@@ -592,6 +594,7 @@ struct sbd_engine_s {
     std::vector<Slot> slots;
     int64_t next_id = 0;
     size_t bytes_in_use = 0, bytes_peak = 0;
+    double vtime = 0.0;  // fair schedule: smallest pass of the running jobs at the last iteration
     int64_t max_chunks = 0;
     // device staging block: header, slot descriptors, chunk table (+ pinned host mirror)
     size_t off_hdr = 0, off_slots = 0, off_cslot = 0, off_coff = 0, stage_bytes = 0;
@@ -792,10 +795,14 @@ bool sbd_engine_s::admit_one()
         return false;
     }
     pending.pop_front();
+    double pass0 = vtime;  // a new job starts at the smallest pass of the running ones
+    for (const Slot &r : slots)
+        if (r.job) pass0 = std::min(pass0, r.pass);
     Slot &s = slots[free_idx];
     s = Slot{};
     s.job = j;
     s.N = N;
+    s.pass = pass0;
     j->res.t_admit = now_seconds(t0);
     j->res.ndets = N;
     try {
@@ -1110,11 +1117,28 @@ int sbd_engine_s::step()
     if (!gA) capture();
     steps++;
 
-    // graph A: Rayleigh-Ritz for every slot with a basis
+    // the jobs of this iteration: all, or (fair schedule) those within one smallest-job quantum of
+    // the smallest pass (stride scheduling by N; the slot with the smallest pass always runs)
+    {
+        double pmin = INFINITY;
+        int64_t nmin = INT64_MAX;
+        for (const Slot &s : slots)
+            if (s.job) {
+                pmin = std::min(pmin, s.pass);
+                nmin = std::min(nmin, s.N);
+            }
+        vtime = pmin;
+        for (Slot &s : slots) {
+            s.run = s.job && (opt.schedule == SBD_SCHED_LOCKSTEP || s.pass < pmin + (double)std::max<int64_t>(nmin, 1));
+            if (s.run) s.pass += (double)s.N;
+        }
+    }
+
+    // graph A: Rayleigh-Ritz for every running slot with a basis
     bool anyA = false;
     for (Slot &s : slots) {
         s.kind = 0;
-        if (s.job && s.k >= 1) {
+        if (s.run && s.k >= 1) {
             s.kind = kRitz;
             anyA = true;
         }
@@ -1126,7 +1150,7 @@ int sbd_engine_s::step()
     // decisions
     for (int i = 0; i < (int)slots.size(); ++i) {
         Slot &s = slots[i];
-        if (!s.job) continue;
+        if (!s.run) continue;
         Job *j = s.job;
         if (s.k == 0) {
             s.kind = kGrow;  // seed: the initial unit vector enters the basis
@@ -1160,7 +1184,7 @@ int sbd_engine_s::step()
     }
     // graph B
     bool anyB = false;
-    for (Slot &s : slots) anyB |= s.job && s.kind;
+    for (Slot &s : slots) anyB |= s.run && s.kind;
     if (anyB) {
         write_stage();
         build_sigma_lists();
@@ -1168,7 +1192,7 @@ int sbd_engine_s::step()
     }
     for (int i = 0; i < (int)slots.size(); ++i) {
         Slot &s = slots[i];
-        if (!s.job || !s.kind) continue;
+        if (!s.run || !s.kind) continue;
         Job *j = s.job;
         const Status &st = hstatus[i];
         if (s.kind & kGrow) {
@@ -1245,6 +1269,7 @@ void sbd_engine_default_options(sbd_engine_options *o)
     o->rows_per_item = 0;
     o->delta = 1e-4;
     o->table_bytes_per_string = 16384;
+    o->schedule = SBD_SCHED_FAIR;
 }
 
 int sbd_engine_create(sbd_engine *out, const sbd_engine_options *opt, void *stream)
@@ -1259,7 +1284,7 @@ int sbd_engine_create(sbd_engine *out, const sbd_engine_options *opt, void *stre
         o.max_strings > (int)kMaxStringsPerSpin || !(o.rows_per_item == 0 || o.rows_per_item == 1 ||
                                                      o.rows_per_item == 2 || o.rows_per_item == 4 ||
                                                      o.rows_per_item == 8) ||
-        !(o.delta > 0.0)) {
+        !(o.delta > 0.0) || !(o.schedule == SBD_SCHED_FAIR || o.schedule == SBD_SCHED_LOCKSTEP)) {
         set_thread_error("invalid engine options");
         return SBD_ERR_INVALID_ARG;
     }

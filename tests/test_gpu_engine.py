@@ -149,6 +149,29 @@ def test_engine_results_are_bitwise_the_same_alone_and_in_a_mix(B, alone):
             assert np.array_equal(e.vector(j, r["ndets"]), va)
 
 
+def test_engine_schedules_give_the_same_results(B, alone):
+    # fair (by cost) and lockstep schedules differ only in which jobs take part in an iteration:
+    # every job's results are bitwise those of its solve alone; the fair schedule runs more, smaller
+    # iterations, and its smallest job is done no later than its largest
+    jobs = _small_jobs()
+    out = {}
+    for sched in ("fair", "lockstep"):
+        with _engine(B, schedule=sched) as e:
+            ids = [e.submit(wl, tol=TOL, tol_energy=TOL_E, keep_vector=True) for wl in jobs]
+            e.run()
+            res = [e.result(j) for j in ids]
+            for j, r, (ra, va) in zip(ids, res, alone):
+                for key in ("status", "iterations", "sigma_mixed", "sigma_fp64", "restarts", "energy", "residual"):
+                    assert r[key] == ra[key], (sched, key)
+                assert np.array_equal(e.vector(j, r["ndets"]), va)
+            out[sched] = (e.stats()["steps"], res)
+    assert out["fair"][0] > out["lockstep"][0]
+    done = [r["t_done"] for r in out["fair"][1]]
+    assert done[0] <= done[-1]
+    with pytest.raises(ValueError):
+        _engine(B, schedule="round-robin")
+
+
 def _estimate(wl, max_sub=12):
     # the engine's admission estimate: basis and vectors, diagonal + work vector, table reserve
     return wl.ndets * (8 * (2 * max_sub + 3) + 4 + 16) + 16384 * (wl.A.size + wl.B.size)
