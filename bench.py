@@ -349,7 +349,7 @@ def engine_line(args, metric_value, elapsed, n_jobs, stats, extra, clk, config):
             "graph_launches": int(stats["graph_launches"]), "engine": stats, "clocks": clk, **extra}
 
 
-def batch_measure(B, insts, subspace: int, warmup: int, steps: int, schedule: str = "fair") -> dict:
+def batch_measure(B, insts, subspace: int, warmup: int, steps: int, schedule: str = "lockstep") -> dict:
     """One engine run over `insts` (persistent launches, CUDA graphs), `steps` times after `warmup`
     untimed runs on the two smallest instances, against the serial FP64 per-instance path on the
     same instances and stopping rule.  solves/s count converged jobs only (status 0)."""
@@ -412,7 +412,7 @@ def run_batch(args):
     insts = W.batch_instances(args.batch_n)
     clocks = ClockSampler(0)
     clocks.start()
-    m = batch_measure(B, insts, args.engine_subspace, args.warmup, args.steps, args.engine_schedule)
+    m = batch_measure(B, insts, args.engine_subspace, args.warmup, args.steps, args.batch_schedule)
     clk = clocks.stop()
     extra = {"batch": m["summary"], "vs_serial_fp64": m["vs_serial_fp64"]}
     config = {"workload": f"batch{len(insts)}: {len(insts)} instances, norb in {{16,20,24,26}}, "
@@ -546,7 +546,7 @@ def run_serve(args):
     clocks = ClockSampler(0)
     clocks.start()
     m = serve_measure(B, built, traces, rates, args.engine_subspace, int(args.budget_gb * 1e9),
-                      max(args.max_strings, 15000 if args.serve_big else 0), args.warmup, args.engine_schedule)
+                      max(args.max_strings, 15000 if args.serve_big else 0), args.warmup, args.serve_schedule)
     clk = clocks.stop()
     m["serving"]["job_build_s"] = t_build
     extra = {"serving": m["serving"], "vs_serial_fp64": m["vs_serial_fp64"]}
@@ -677,9 +677,10 @@ def main():
     ap.add_argument("--max-strings", type=int, default=5000, help="largest |A| = |B| of the serve workload")
     ap.add_argument("--budget-gb", type=float, default=160.0, help="engine admission budget of the serve workload")
     ap.add_argument("--engine-subspace", type=int, default=20, help="Davidson basis per job in the engine")
-    ap.add_argument("--engine-schedule", default="fair",
-                    help="engine iterations: jobs share the device by cost (fair) or all jobs every iteration "
-                         "(lockstep); the serve workload takes a comma-separated list (one engine run each)")
+    ap.add_argument("--engine-schedule", default="",
+                    help="engine iterations: jobs share the device by cost (fair; default for serving, where "
+                         "latency counts) or all jobs every iteration (lockstep; default for the batched "
+                         "workload, submitted at once); the serve workload takes a comma-separated list")
     ap.add_argument("--serve-big", type=int, default=0,
                     help="serve workload: the last N jobs at norb 58, |A|=|B|=15,000 (the top of its range)")
     ap.add_argument("--legs", default="batch,serve",
@@ -690,8 +691,10 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     scheds = [x for x in args.engine_schedule.split(",") if x]
-    if not scheds or any(x not in ("fair", "lockstep") for x in scheds) or (len(scheds) > 1 and args.workload != "serve"):
+    if any(x not in ("fair", "lockstep") for x in scheds) or (len(scheds) > 1 and args.workload != "serve"):
         ap.error("--engine-schedule: fair or lockstep (a comma-separated list only for --workload serve)")
+    args.batch_schedule = args.engine_schedule or "lockstep"
+    args.serve_schedule = args.engine_schedule or "fair"
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch64":
@@ -914,7 +917,7 @@ def main():
         want = {x.strip() for x in args.legs.split(",") if x.strip()}
         if "batch" in want:
             insts = W.batch_instances(64)[: args.leg_batch_n]
-            m = batch_measure(B, insts, args.engine_subspace, warmup=1, steps=1, schedule=args.engine_schedule)
+            m = batch_measure(B, insts, args.engine_subspace, warmup=1, steps=1, schedule=args.batch_schedule)
             legs["batch"] = {"workload": f"the first {len(insts)} of the 64 batched instances (norb in "
                                          f"{{16,20,24,26}}, |A|,|B| in [500,5000])",
                              "engine_mixed": m["summary"], "serial_fp64": m["vs_serial_fp64"],
@@ -922,7 +925,7 @@ def main():
         if "serve" in want:
             traces, built, _ = serve_jobs(args.leg_requests, [args.rate], 5000)
             m = serve_measure(B, built, traces, [args.rate], args.engine_subspace, int(args.budget_gb * 1e9), 5000,
-                              warmup=1, schedule=args.engine_schedule)
+                              warmup=1, schedule=args.serve_schedule)
             legs["serve"] = {"workload": f"{args.leg_requests} Poisson arrivals at {args.rate:g}/s, norb in "
                                          f"{{24,32,40,48,58}}, |A|=|B| log-uniform in [300,5000], "
                                          f"{args.budget_gb:g} GB budget",
