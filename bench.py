@@ -301,16 +301,18 @@ def run_reference(args):
 
 def kernel_source_digest() -> str:
     """sha256 prefix of the mixed alpha-beta pass's source (the column-stationary kernel: its chunk,
-    table and row device functions) and of the code that lays out the source-major singles it walks
-    (the item order decides which rows of C it reads when)."""
+    table and row device functions) and of the four kernels that lay out the source-major singles it
+    walks (the item order decides which rows of C it reads when)."""
     csrc = os.path.join(ROOT, "paper_2601_16637_gb300", "csrc")
     src = open(os.path.join(csrc, "sigma.cu")).read()
     start = src.index("template <int KC>\n__device__ __forceinline__ void src_chunk(")
     end = src.index("\n}\n", src.index("__global__ void __launch_bounds__(kSrcThreads, 1) ab_src_kernel(")) + 3
     tab = open(os.path.join(csrc, "tables.cu")).read()
-    t0 = tab.index("__global__ void src_count_kernel(")
-    t1 = tab.index("\n}\n", tab.index("__global__ void src_entry_order_kernel(")) + 3
-    return hashlib.sha256((src[start:end] + tab[t0:t1]).encode()).hexdigest()[:16]
+    parts = []
+    for name in ("src_count_kernel(", "src_fill_kernel(", "src_slice_order_kernel(", "src_entry_order_kernel("):
+        t0 = tab.index("__global__ void " + name)
+        parts.append(tab[t0:tab.index("\n}\n", t0) + 3])
+    return hashlib.sha256((src[start:end] + "".join(parts)).encode()).hexdigest()[:16]
 
 
 def traffic_record(kernel: str):
