@@ -80,6 +80,13 @@ def test_engine_defaults_and_argument_errors_need_no_gpu(lib):
     bad = b.sbd_engine_default_options()
     bad.rows_per_item = 3
     assert lib.sbd_engine_create(ctypes.byref(out), ctypes.byref(bad), None) == -1
+    # schedule: 0 fair share by cost (default), 1 lockstep; anything else is refused
+    assert o.schedule == b.SCHEDULE["fair"] == 0 and b.SCHEDULE["lockstep"] == 1
+    bad = b.sbd_engine_default_options()
+    bad.schedule = 2
+    assert lib.sbd_engine_create(ctypes.byref(out), ctypes.byref(bad), None) == -1
+    with pytest.raises(ValueError):
+        b.Engine(schedule="round-robin")
     assert lib.sbd_engine_create(None, None, None) == -1
     assert lib.sbd_engine_destroy(None) == -1
     assert lib.sbd_engine_step(None, None) == -1

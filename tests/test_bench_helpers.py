@@ -70,3 +70,17 @@ def test_energy_error_estimate_uses_the_distance_to_the_next_ritz_value():
     assert abs(est[1] - 4e-8 / (0.5 + 0.25)) < 1e-20
     assert abs(est[2] - 9e-8 / 0.5) < 1e-20
     assert bench.energy_error_estimates(e, r, {"gap_estimate": 0.0}) == [None, None, None]
+
+
+def test_engine_schedule_option_is_checked_before_any_gpu_work():
+    import subprocess
+
+    def run(*extra):
+        return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *extra], cwd=ROOT,
+                              capture_output=True, text=True, timeout=120)
+
+    r = run("--engine-schedule", "round-robin")
+    assert r.returncode == 2 and "--engine-schedule" in r.stderr
+    # a list of schedules is only for the serve workload (one engine run each)
+    r = run("--engine-schedule", "fair,lockstep")
+    assert r.returncode == 2 and "--engine-schedule" in r.stderr
