@@ -305,7 +305,7 @@ def kernel_source_digest() -> str:
     walks (the item order decides which rows of C it reads when)."""
     csrc = os.path.join(ROOT, "paper_2601_16637_gb300", "csrc")
     src = open(os.path.join(csrc, "sigma.cu")).read()
-    start = src.index("template <int KC>\n__device__ __forceinline__ void src_chunk(")
+    start = src.index("template <int KC, int RS>\n__device__ __forceinline__ void src_chunk(")
     end = src.index("\n}\n", src.index("__global__ void __launch_bounds__(kSrcThreads, 1) ab_src_kernel(")) + 3
     tab = open(os.path.join(csrc, "tables.cu")).read()
     parts = []

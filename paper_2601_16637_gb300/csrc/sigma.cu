@@ -799,6 +799,9 @@ __global__ void __launch_bounds__(Threads<T>::value) ab_pass_kernel(const AbArgs
 // (step + l) mod 8 at each step, so the 8 lanes of a 128-bit phase hit 8 distinct bank groups
 // whatever rows they read; with KC = 16 (8) each row holds 2 (4) copies and lanes read their own
 // copy, rotated within it.  The lane's registers hold the amplitudes in the same rotated order.
+// For large norb the rows are 64 bytes (RS = 4 chunks, KC <= 16): with KC = 16 a row holds one
+// copy, the rotation spreads lanes l and l + 4 of a phase over the same four chunks, and two of
+// them conflict when their rows lie in the same half of the 128-byte bank window.
 //
 // Determinism: each FP32 dot product is rounded once onto a fixed-point grid with one scale 2^e per
 // output row and added as an integer, and integer addition is exact and order independent, so the
@@ -830,13 +833,21 @@ struct AbSrcArgs {
     const float *rowmax;      // [nA] max |C(ja, :)|
     float bound;              // maxdeg_beta * max |(pq|rs)|
     int maxdeg;               // maxdeg_beta: most singles of a beta string
+    int rs;                   // W row stride in float4: 8 (chunks of up to 32 alpha singles) or 4 (up to 16)
 };
 
-// shared memory of one CTA: W [npair][8] float4, accumulator [nB] u64, pair -> rs code
-__host__ __device__ constexpr size_t src_w_bytes(int npair) { return (size_t)npair * 128; }
-__host__ __device__ inline size_t src_smem(int npair, int64_t nB)
+// shared memory of one CTA: W [npair][rs] float4, accumulator [nB] u64, pair -> rs code.  rs = 4
+// (64-byte W rows, chunks of at most 16 alpha singles) is the layout for large norb, where the
+// 128-byte rows and the row accumulator do not fit together (norb 58: 1,653 pairs, 211 KB of rows)
+__host__ __device__ constexpr size_t src_w_bytes(int npair, int rs) { return (size_t)npair * rs * 16; }
+__host__ __device__ inline size_t src_smem(int npair, int64_t nB, int rs)
 {
-    return src_w_bytes(npair) + (size_t)nB * 8 + round16((size_t)npair * 2);
+    return src_w_bytes(npair, rs) + (size_t)nB * 8 + round16((size_t)npair * 2);
+}
+// the W row stride that fits `limit` bytes (8 preferred), 0 if neither does
+__host__ __device__ inline int src_rs(int npair, int64_t nB, size_t limit)
+{
+    return src_smem(npair, nB, 8) <= limit ? 8 : (src_smem(npair, nB, 4) <= limit ? 4 : 0);
 }
 
 // adds t * f to element ib of the row accumulator (words lo[ib], hi[ib]; see above)
@@ -850,15 +861,16 @@ __device__ __forceinline__ void src_add(unsigned *acc_lo, unsigned *acc_hi, uint
     atomicAdd(acc_hi + ib, (unsigned)(int)(v >> lbits));
 }
 
-template <int KC>
+template <int KC, int RS>
 __device__ __forceinline__ void src_chunk(const AbSrcArgs &a, const float4 *__restrict__ Wt, unsigned *acc_lo,
                                           unsigned *acc_hi, const int *ja_s, int kc, float scale, int lbits,
                                           int *ctr)
 {
+    static_assert(KC / 4 <= RS, "a W row holds at least one copy of the chunk");
     constexpr int CPW = KC / 4;  // 16-byte chunks per copy of a W row
     const int lane = threadIdx.x & 31;
     const int rot = lane & (CPW - 1);
-    const int base = ((lane / CPW) & (8 / CPW - 1)) * CPW;  // first chunk of this lane's copy
+    const int base = ((lane / CPW) & (RS / CPW - 1)) * CPW;  // first chunk of this lane's copy
     const int nsl = (int)((a.src_nitem + 31) >> 5);
     while (true) {
         int sl = 0;
@@ -902,8 +914,8 @@ __device__ __forceinline__ void src_chunk(const AbSrcArgs &a, const float4 *__re
         for (int i = 0; i < kSrcItem; i += 2) {  // two singles per round for independent chains
             if (i < cnt) {
                 const bool two = i + 1 < cnt;
-                const float4 *w0 = Wt + ((e[i] >> kSrcPairShift) & 0x7ffu) * 8 + base;
-                const float4 *w1 = Wt + ((e[i + 1] >> kSrcPairShift) & 0x7ffu) * 8 + base;
+                const float4 *w0 = Wt + ((e[i] >> kSrcPairShift) & 0x7ffu) * RS + base;
+                const float4 *w1 = Wt + ((e[i + 1] >> kSrcPairShift) & 0x7ffu) * RS + base;
                 float f0 = 0.f, f1 = 0.f;
 #pragma unroll
                 for (int s = 0; s < CPW; ++s) {
@@ -927,13 +939,13 @@ __device__ __forceinline__ void src_chunk(const AbSrcArgs &a, const float4 *__re
 }
 
 // W[x][position p] for the chunk's alpha singles, position p holding amplitude chunk p mod CPW
-template <int KC>
+template <int KC, int RS>
 __device__ __forceinline__ void src_build_w(const AbSrcArgs &a, float4 *Wt, const int16_t *rs_of,
                                             const int *pq_s, const float *u_s, int kc)
 {
     constexpr int CPW = KC / 4;
     const int n2 = a.norb * a.norb;
-    for (int idx = threadIdx.x; idx < a.npair * 8; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < a.npair * RS; idx += blockDim.x) {
         const int p = idx / a.npair, x = idx - p * a.npair;
         const int c = p & (CPW - 1);
         const int rs = rs_of[x];
@@ -943,16 +955,18 @@ __device__ __forceinline__ void src_build_w(const AbSrcArgs &a, float4 *Wt, cons
             const int k = 4 * c + i;
             v[i] = k < kc ? u_s[k] * __ldg(a.eri + (size_t)pq_s[k] * n2 + rs) : 0.f;
         }
-        Wt[(size_t)x * 8 + p] = make_float4(v[0], v[1], v[2], v[3]);
+        Wt[(size_t)x * RS + p] = make_float4(v[0], v[1], v[2], v[3]);
     }
 }
 
+template <int RS>
 __device__ __forceinline__ void src_row(const AbSrcArgs &a, int64_t ia, unsigned char *smem)
 {
+    constexpr int KMAX = RS * 4;  // alpha singles per chunk
     float4 *Wt = reinterpret_cast<float4 *>(smem);
-    unsigned *acc_lo = reinterpret_cast<unsigned *>(smem + src_w_bytes(a.npair));
+    unsigned *acc_lo = reinterpret_cast<unsigned *>(smem + src_w_bytes(a.npair, RS));
     unsigned *acc_hi = acc_lo + a.nB;
-    const int16_t *rs_of = reinterpret_cast<const int16_t *>(smem + src_w_bytes(a.npair) + (size_t)a.nB * 8);
+    const int16_t *rs_of = reinterpret_cast<const int16_t *>(smem + src_w_bytes(a.npair, RS) + (size_t)a.nB * 8);
     __shared__ __align__(16) int ja_s[32];
     __shared__ int pq_s[32];
     __shared__ float u_s[32];
@@ -967,7 +981,7 @@ __device__ __forceinline__ void src_row(const AbSrcArgs &a, int64_t ia, unsigned
     __syncthreads();  // the previous row is finished with shared memory
     for (int64_t ib = tid; ib < a.nB; ib += blockDim.x) acc_lo[ib] = acc_hi[ib] = 0u;
     {
-        int16_t *rs_w = reinterpret_cast<int16_t *>(smem + src_w_bytes(a.npair) + (size_t)a.nB * 8);
+        int16_t *rs_w = reinterpret_cast<int16_t *>(smem + src_w_bytes(a.npair, RS) + (size_t)a.nB * 8);
         for (int r = 1; r < a.norb; ++r)
             for (int s = tid; s < r; s += blockDim.x) rs_w[r * (r - 1) / 2 + s] = (int16_t)(r * a.norb + s);
     }
@@ -984,7 +998,7 @@ __device__ __forceinline__ void src_row(const AbSrcArgs &a, int64_t ia, unsigned
                 s_state = 0;
             } else {
                 // contributions per element: at most maxdeg per chunk of the row
-                const long long m = (long long)max(a.maxdeg, 1) * ((K + 31) / 32);
+                const long long m = (long long)max(a.maxdeg, 1) * ((K + KMAX - 1) / KMAX);
                 const int lbits = max(1, 32 - (64 - __clzll(m)));
                 int e = 30 + lbits - ilogb(bnd) - 1;  // bnd < 2^(ilogb+1), so bnd * 2^e < 2^(30+lbits)
                 e = max(-120, min(120, e));
@@ -1004,8 +1018,8 @@ __device__ __forceinline__ void src_row(const AbSrcArgs &a, int64_t ia, unsigned
     }
     const float scale = s_scale;
     const int lbits = s_lbits;
-    for (int k0 = 0; k0 < K; k0 += 32) {
-        const int kc = min(32, K - k0);
+    for (int k0 = 0; k0 < K; k0 += KMAX) {
+        const int kc = min(KMAX, K - k0);
         __syncthreads();  // the previous chunk is finished with W and the chunk arrays
         if (tid < kc) {
             const uint32_t pk = a.as_pk[e0 + k0 + tid];
@@ -1016,17 +1030,17 @@ __device__ __forceinline__ void src_row(const AbSrcArgs &a, int64_t ia, unsigned
         if (tid == 0) ctr = 0;
         __syncthreads();
         if (kc <= 8) {
-            src_build_w<8>(a, Wt, rs_of, pq_s, u_s, kc);
+            src_build_w<8, RS>(a, Wt, rs_of, pq_s, u_s, kc);
             __syncthreads();
-            src_chunk<8>(a, Wt, acc_lo, acc_hi, ja_s, kc, scale, lbits, &ctr);
-        } else if (kc <= 16) {
-            src_build_w<16>(a, Wt, rs_of, pq_s, u_s, kc);
+            src_chunk<8, RS>(a, Wt, acc_lo, acc_hi, ja_s, kc, scale, lbits, &ctr);
+        } else if (RS == 4 || kc <= 16) {
+            src_build_w<16, RS>(a, Wt, rs_of, pq_s, u_s, kc);
             __syncthreads();
-            src_chunk<16>(a, Wt, acc_lo, acc_hi, ja_s, kc, scale, lbits, &ctr);
+            src_chunk<16, RS>(a, Wt, acc_lo, acc_hi, ja_s, kc, scale, lbits, &ctr);
         } else {
-            src_build_w<32>(a, Wt, rs_of, pq_s, u_s, kc);
+            src_build_w<(RS == 8 ? 32 : 16), RS>(a, Wt, rs_of, pq_s, u_s, kc);
             __syncthreads();
-            src_chunk<32>(a, Wt, acc_lo, acc_hi, ja_s, kc, scale, lbits, &ctr);
+            src_chunk<(RS == 8 ? 32 : 16), RS>(a, Wt, acc_lo, acc_hi, ja_s, kc, scale, lbits, &ctr);
         }
     }
     __syncthreads();
@@ -1037,10 +1051,12 @@ __device__ __forceinline__ void src_row(const AbSrcArgs &a, int64_t ia, unsigned
     }
 }
 
+// one instance per W row stride (the host launches the one a.rs names)
+template <int RS>
 __global__ void __launch_bounds__(kSrcThreads, 1) ab_src_kernel(const AbSrcArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    for (int64_t ia = blockIdx.x; ia < a.nA; ia += gridDim.x) src_row(a, ia, smem);
+    for (int64_t ia = blockIdx.x; ia < a.nA; ia += gridDim.x) src_row<RS>(a, ia, smem);
 }
 
 // out[c][r] = in[r][c]; with rowmax (FP32 only, zeroed beforehand): rowmax[r] = max_c |in[r][c]|,
@@ -1110,11 +1126,13 @@ __global__ void absmax_kernel(const float *__restrict__ x, int64_t n, unsigned *
 
 int npairs(int norb) { return norb * (norb - 1) / 2; }
 
-// the column-stationary alpha-beta pass applies when its W table and row accumulator fit
-bool src_fits(const Ctx &c)
+// the column-stationary alpha-beta pass applies when its W table (128- or 64-byte rows) and row
+// accumulator fit
+int src_rs_of(const Ctx &c)
 {
-    return c.norb >= 2 && c.sp[1].src_ent && src_smem(npairs(c.norb), c.nB) <= smem_limit(c);
+    return (c.norb >= 2 && c.sp[1].src_ent) ? src_rs(npairs(c.norb), c.nB, smem_limit(c)) : 0;
 }
+bool src_fits(const Ctx &c) { return src_rs_of(c) > 0; }
 
 AbSrcArgs src_args(const Ctx &c, const float *C, double *S, const float *rowmax)
 {
@@ -1135,13 +1153,15 @@ AbSrcArgs src_args(const Ctx &c, const float *C, double *S, const float *rowmax)
     a.rowmax = rowmax;
     a.bound = (float)((double)tb.src_maxdeg * (double)c.eri_absmax);
     a.maxdeg = tb.src_maxdeg;
+    a.rs = src_rs_of(c);
     return a;
 }
 
 void launch_ab_src(const AbSrcArgs &a, int num_sms, cudaStream_t s)
 {
     const int grid = (int)std::min<int64_t>(a.nA, (int64_t)num_sms);
-    ab_src_kernel<<<grid, kSrcThreads, src_smem(a.npair, a.nB), s>>>(a);
+    if (a.rs == 8) ab_src_kernel<8><<<grid, kSrcThreads, src_smem(a.npair, a.nB, 8), s>>>(a);
+    else ab_src_kernel<4><<<grid, kSrcThreads, src_smem(a.npair, a.nB, 4), s>>>(a);
     SBD_LAUNCH("ab_src_kernel");
 }
 
@@ -1485,13 +1505,14 @@ __global__ void __launch_bounds__(Threads<T>::value) ab_batch_kernel(const int *
     item_loop(pn, off, args, counter, sa, [&](int64_t li) { ab_row<T, R, true>(sa, li, smem); });
 }
 
+template <int RS>
 __global__ void __launch_bounds__(kSrcThreads, 1) ab_src_batch_kernel(const int *pn, const int64_t *off,
                                                                       const AbSrcArgs *args,
                                                                       unsigned long long *counter)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ AbSrcArgs sa;
-    item_loop(pn, off, args, counter, sa, [&](int64_t li) { src_row(sa, li, smem); });
+    item_loop(pn, off, args, counter, sa, [&](int64_t li) { src_row<RS>(sa, li, smem); });
 }
 
 __global__ void __launch_bounds__(Threads<float>::value) row_halves_batch_kernel(const int *pn, const int64_t *off,
@@ -1516,6 +1537,7 @@ struct SigmaBatch {
     int max_slots = 0, R = 1, device = 0, grid_pass = 0, grid_t = 0, grid_src = 0;
     size_t smem = 0;
     bool src = false;     // mixed: the column-stationary alpha-beta pass (when its table and accumulator fit)
+    int src_rs = 0;       // its W row stride for the largest slot (8 or 4 float4)
     size_t src_smem = 0;
     Layout L{};
     unsigned char *dev = nullptr, *host = nullptr;
@@ -1546,7 +1568,9 @@ void batch_set(SigmaBatch *b, const SigmaSlot *slots, int n)
         if constexpr (std::is_same<T, float>::value) {
             if (b->src) {
                 rb[i].rowmax = c.rowmax;
-                reinterpret_cast<AbSrcArgs *>(h + L.src)[i] = src_args(c, x, sl.y, c.rowmax);
+                AbSrcArgs sa = src_args(c, x, sl.y, c.rowmax);
+                sa.rs = b->src_rs;  // every slot in the layout the batch's shared memory was sized for
+                reinterpret_cast<AbSrcArgs *>(h + L.src)[i] = sa;
             }
         }
         td[i] = TDesc<E>{x, xt, c.nA, c.nB};
@@ -1588,9 +1612,12 @@ void batch_launch_r(SigmaBatch *b, cudaStream_t s)
         SBD_LAUNCH("row_batch_kernel");
     }
     if (std::is_same<T, float>::value && b->src) {
-        ab_src_batch_kernel<<<b->grid_src, kSrcThreads, b->src_smem, s>>>(
-            pn, reinterpret_cast<const int64_t *>(d + L.off_ab), reinterpret_cast<const AbSrcArgs *>(d + L.src),
-            b->counters + 2);
+        const int64_t *off_ab = reinterpret_cast<const int64_t *>(d + L.off_ab);
+        const AbSrcArgs *src_args_d = reinterpret_cast<const AbSrcArgs *>(d + L.src);
+        if (b->src_rs == 8)
+            ab_src_batch_kernel<8><<<b->grid_src, kSrcThreads, b->src_smem, s>>>(pn, off_ab, src_args_d, b->counters + 2);
+        else
+            ab_src_batch_kernel<4><<<b->grid_src, kSrcThreads, b->src_smem, s>>>(pn, off_ab, src_args_d, b->counters + 2);
         SBD_LAUNCH("ab_src_batch_kernel");
         return;
     }
@@ -1623,10 +1650,18 @@ void batch_attrs(SigmaBatch *b)
     b->grid_pass = sms * occ;
     b->grid_t = sms * 8;
     if (b->src) {
-        SBD_CUDA(cudaFuncSetAttribute(ab_src_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)b->src_smem));
         int occ_src = 0;
-        SBD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_src, ab_src_batch_kernel, kSrcThreads, b->src_smem));
+        if (b->src_rs == 8) {
+            SBD_CUDA(cudaFuncSetAttribute(ab_src_batch_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)b->src_smem));
+            SBD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_src, ab_src_batch_kernel<8>, kSrcThreads,
+                                                                   b->src_smem));
+        } else {
+            SBD_CUDA(cudaFuncSetAttribute(ab_src_batch_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)b->src_smem));
+            SBD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_src, ab_src_batch_kernel<4>, kSrcThreads,
+                                                                   b->src_smem));
+        }
         b->grid_src = sms * std::max(1, occ_src);
     }
 }
@@ -1641,7 +1676,8 @@ void sigma_prepare(Ctx &c)
     set_attrs<double>(lim);
     set_attrs<float>(lim);
     set_attrs<F2>(lim);
-    SBD_CUDA(cudaFuncSetAttribute(ab_src_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    SBD_CUDA(cudaFuncSetAttribute(ab_src_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    SBD_CUDA(cudaFuncSetAttribute(ab_src_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     SBD_CUDA(cudaFuncSetAttribute(row_halves_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     // max |(pq|rs)| of the FP32 integrals, for the fixed-point scale of the alpha-beta pass
     const int64_t n4 = (int64_t)c.norb * c.norb * c.norb * c.norb;
@@ -1666,7 +1702,7 @@ bool sigma_batch_fits(sbd_precision prec, int R, int max_strings, int max_norb, 
     const size_t lim = sigma_batch_smem_limit(device);
     if (R == kHalfRows)
         return prec == SBD_MIXED && max_norb >= 2 && sigma_batch_smem(prec, R, max_strings, max_norb) <= lim &&
-               src_smem(npairs(max_norb), max_strings) <= lim;
+               src_rs(npairs(max_norb), max_strings, lim) > 0;
     if (R == 4 && prec != SBD_MIXED) return false;
     return sigma_batch_smem(prec, R, max_strings, max_norb) <= lim;
 }
@@ -1693,8 +1729,9 @@ SigmaBatch *sigma_batch_create(int max_slots, sbd_precision prec, int R, int max
     b->R = R;
     b->device = device;
     b->smem = smem;
-    b->src_smem = src_smem(npairs(max_norb), max_strings);
-    b->src = prec == SBD_MIXED && max_norb >= 2 && b->src_smem <= sigma_batch_smem_limit(device);
+    b->src_rs = max_norb >= 2 ? src_rs(npairs(max_norb), max_strings, sigma_batch_smem_limit(device)) : 0;
+    b->src_smem = b->src_rs ? src_smem(npairs(max_norb), max_strings, b->src_rs) : 0;
+    b->src = prec == SBD_MIXED && b->src_rs > 0;
     if (R == kHalfRows && !b->src) {
         delete b;
         fail(SBD_ERR_UNSUPPORTED, "batched sigma: 8 rows per item need the column-stationary alpha-beta pass, "
