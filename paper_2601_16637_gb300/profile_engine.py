@@ -15,6 +15,7 @@ def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=8)
     ap.add_argument("--subspace", type=int, default=20)
+    ap.add_argument("--schedule", default="lockstep", choices=["lockstep", "fair"])
     args = ap.parse_args()
 
     import torch
@@ -26,14 +27,14 @@ def main() -> None:
     insts = W.batch_instances(64)[: args.n]
     t0 = time.perf_counter()
     with B.Engine(max_slots=len(insts), max_subspace=args.subspace, max_norb=26, max_strings=5000,
-                  max_iter=400) as e:
+                  max_iter=400, schedule=args.schedule) as e:
         ids = [e.submit(w, tol=w.tol, tol_energy=w.extra["tol_energy"]) for w in insts]
         e.run()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         res = [e.result(j) for j in ids]
         st = e.stats()
-    print(json.dumps({"instances": len(insts), "seconds": dt, "engine": st,
+    print(json.dumps({"instances": len(insts), "schedule": args.schedule, "seconds": dt, "engine": st,
                       "iterations": [r["iterations"] for r in res], "status": [r["status"] for r in res],
                       "energies": [r["energy"] for r in res]}))
 
