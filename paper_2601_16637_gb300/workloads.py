@@ -180,6 +180,10 @@ CONFIGS = {
     # same kernels and launch shapes, a smaller footprint for profiler captures
     "cfg3-6000": dict(norb=29, nalpha=10, nbeta=10, nA=6000, nB=6000, lam=0.25, seed=2,
                       nroots=1, tol=1e-6, precision="mixed", max_subspace=24),
+    # a job from the top of the serving range (norb 58, 19+19 electrons, |A| = |B| = 15,000: 2.25e8
+    # determinants), for profiling the large-norb kernels (with --strings for a smaller capture)
+    "serve-top": dict(norb=58, nalpha=19, nbeta=19, nA=15000, nB=15000, lam=0.35, seed=77,
+                      nroots=1, tol=1e-4, precision="mixed", max_subspace=20),
 }
 
 
