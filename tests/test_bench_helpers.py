@@ -84,3 +84,15 @@ def test_engine_schedule_option_is_checked_before_any_gpu_work():
     # a list of schedules is only for the serve workload (one engine run each)
     r = run("--engine-schedule", "fair,lockstep")
     assert r.returncode == 2 and "--engine-schedule" in r.stderr
+
+
+def test_serve_trace_with_jobs_from_the_top_of_the_range():
+    # --serve-big n replaces the last n jobs of the seeded trace by jobs of the top of the range, at
+    # the same arrival times; the others are the trace's own jobs
+    traces, built, _ = bench.serve_jobs(6, [20.0], 400, big=2, big_strings=300, big_norb=20)
+    plain, built0, _ = bench.serve_jobs(6, [20.0], 400)
+    assert [t for t, _, _ in traces[20.0]] == [t for t, _, _ in plain[20.0]]
+    for w, w0 in zip(built[:4], built0[:4]):
+        assert (w.norb, w.A.size, w.B.size) == (w0.norb, w0.A.size, w0.B.size)
+    for w in built[4:]:
+        assert w.norb == 20 and w.nalpha == w.nbeta == 7 and w.A.size == w.B.size == 300
